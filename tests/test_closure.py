@@ -1,0 +1,93 @@
+"""Closure of binned reweighting against a direct continuum fold (paper Sec. VI.A).
+
+The paper's worked example: a 7Be line (0.862 MeV), a response with 500
+photoelectrons/MeV, a quenched light yield and Gaussian photoelectron
+statistics sigma = sqrt(<N_p>), ROI 50 < N_p < 400.  The direct prediction
+folds the modified recoil spectrum through P(N_p | T) on a fine quadrature
+grid; the reweighted prediction bins the SM recoil spectrum, applies one
+weight per recoil bin (eq. fT at the bin centre, eq. reweight_factor) and
+folds through the SM-weighted response matrix (eq. fNp_reweight).
+
+Printed results (Sec. VI.A, Figs. closure and closure_conv): integral
+deviation in the ROI falls as n_T^-2; at 25 bins it is 1.3e-5 (NSI,
+eps_L = eps_R = 0.1) and 9.7e-5 (mu_nu = 2.8e-11 mu_B); at 2000 bins it is
+below 1e-6 with per-bin residuals below 1e-5.  The quenching law is not
+given in the paper (T/(1 + 0.01 MeV/T) here), so the 25-bin values are pinned
+to within a factor of two and the slope to within 5 %.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle as O
+
+E_LINE = 0.862
+T_MIN = 1e-3
+LIGHT_YIELD = 500.0
+NP_EDGES = np.arange(0.0, 501.0, 1.0)
+ROI = slice(51, 400)
+GL_X, GL_W = np.polynomial.legendre.leggauss(16)
+SRC = [{"e": np.array([E_LINE]), "w": np.array([1.0]), "pee": np.array([0.55])}]
+
+
+def _p_np_given_t(t):
+    m = (LIGHT_YIELD * t * t / (t + 0.01))[:, None]
+    s = np.sqrt(np.maximum(m, 1e-12))
+    return np.diff(0.5 * (1.0 + erf((NP_EDGES[None, :] - m) / (math.sqrt(2.0) * s))), axis=1)
+
+
+def _dsigma(t, theta):
+    g = O.nsi_couplings(theta, 0.23121)
+    pe, pm, pt = O.flavor_probabilities(0.55, 0.5)
+    return (pe * O.dsigma_weak(E_LINE, t, *g["e"]) + pm * O.dsigma_weak(E_LINE, t, *g["mu"])
+            + pt * O.dsigma_weak(E_LINE, t, *g["tau"]) + O.dsigma_mm(E_LINE, t, theta[4]))
+
+
+def _integrate(fn, lo, hi, nsub):
+    edges = np.linspace(lo, hi, nsub + 1)
+    tot = 0.0
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = 0.5 * (a + b) + 0.5 * (b - a) * GL_X
+        tot = tot + 0.5 * (b - a) * np.tensordot(GL_W, fn(t), axes=(0, 0))
+    return tot
+
+
+def _direct(theta, tmax):
+    return _integrate(lambda t: _p_np_given_t(t) * _dsigma(t, theta)[:, None], T_MIN, tmax, 4000)
+
+
+def _reweighted(theta, n_t, tmax):
+    edges = np.linspace(0.0, tmax, n_t + 1)
+    e_sm = O.recoil_spectrum(SRC, edges, np.zeros(5), T_MIN)
+    resp = np.zeros((n_t, NP_EDGES.size - 1))
+    for i in range(n_t):
+        a, b = max(edges[i], T_MIN), edges[i + 1]
+        if b <= a or e_sm[i] == 0.0:
+            continue
+        num = _integrate(lambda t: _p_np_given_t(t) * _dsigma(t, np.zeros(5))[:, None], a, b, max(2, 4000 // n_t))
+        resp[i] = num / e_sm[i]
+    r = O.reweight_factor(O.recoil_spectrum(SRC, edges, theta, T_MIN, midpoint=True),
+                          O.recoil_spectrum(SRC, edges, np.zeros(5), T_MIN, midpoint=True))
+    return O.fold(resp.T, r * e_sm)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case,theta,dev25", [
+    ("nsi", np.array([0.1, 0.1, 0.0, 0.0, 0.0]), 1.3e-5),
+    ("mm", np.array([0.0, 0.0, 0.0, 0.0, 2.8]), 9.7e-5),
+])
+def test_closure_matches_paper(case, theta, dev25):
+    tmax = float(O.t_max(E_LINE))
+    d = _direct(theta, tmax)
+    devs = {}
+    for n_t in (25, 50, 100, 2000):
+        mu = _reweighted(theta, n_t, tmax)
+        devs[n_t] = (abs(mu[ROI].sum() - d[ROI].sum()) / d[ROI].sum(), np.max(np.abs(mu[ROI] / d[ROI] - 1.0)))
+    slope = math.log(devs[25][0] / devs[100][0]) / math.log(4.0)
+    assert slope == pytest.approx(2.0, rel=0.05)
+    assert dev25 / 2.0 < devs[25][0] < dev25 * 2.0
+    assert devs[2000][0] < 1e-6
+    assert devs[2000][1] < 1e-5
