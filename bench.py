@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Likelihood evaluations per second on the synthetic solar scan.
+
+One step = one srw_loglik call over a batch of P parameter points on the
+solar-set workload (8003 energy nodes, 4096 recoil bins, 2048 reconstructed
+bins, eight background templates): on-chip weighted spectra, the batched
+response fold, the fused Poisson epilogue and the FP64 per-point reduction,
+replayed from a captured CUDA graph.  Inputs are resident in HBM; L2 is
+flushed (a 256 MiB write) before every timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16|fp32]
+    python bench.py --impl reference ...     # the FP64 oracle on the host cores
+
+Under torchrun each rank evaluates its own batch (weak scaling); the step
+time is the max over ranks and rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "likelihood evals/sec at |d(-2lnL)|<=1e-3 vs FP64 oracle"
+UNIT = "evals/s"
+WORKLOAD_DATA = "solar_set_4096"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="srw", choices=["srw", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "fp32"])
+    ap.add_argument("--points", type=int, default=65536)
+    ap.add_argument("--cpu-sample", type=int, default=12, help="theta points for the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_config(P, precision, extra=None):
+    cfg = {"workload": "solar_scan_%d" % P, "points": P, "n_t": 4096, "n_rec": 2048, "n_nodes": 8003,
+           "n_bkg": 8, "precision": precision, "theta_box": "|eps|<=0.3, mu_hat in [0,3]", "l2": "flushed"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------------------- oracle legs
+def _oracle_sample(P, n, seed):
+    """Run the FP64 oracle on n points of the workload in this process."""
+    import numpy as np
+
+    import workloads
+    from oracle import OracleModel
+    wl = workloads.batched_scan_workload(P, theta_seed=seed)
+    counts = workloads.load_counts(WORKLOAD_DATA)
+    model = OracleModel.from_workload(wl)
+    model.set_data(counts, wl["bkg"])
+    idx = np.linspace(0, P - 1, n).astype(int)
+    t0 = time.perf_counter()
+    vals = model.neg2lnl_batch(wl["theta"][idx].astype(np.float64))
+    dt = time.perf_counter() - t0
+    return idx.tolist(), vals.tolist(), dt
+
+
+def oracle_subprocess(P, n, seed):
+    """The oracle in a fresh single-threaded interpreter (no CUDA state)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_sample(%d, %d, %d)))" % (ROOT, P, n, seed))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
+    idx, vals, dt = json.loads(r.stdout.strip().splitlines()[-1])
+    return idx, vals, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    P = args.points
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_subprocess(P, per_step, 3)
+    times = []
+    for _ in range(args.steps):
+        _, _, dt = oracle_subprocess(P, per_step, 3)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps * per_step / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(P, "fp64", {"reference_sample_per_step": per_step}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d evenly spaced theta of the %d-point batch per step" % (per_step, P)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for r in csv.reader(io.StringIO(open(self.path).read())):
+            if len(r) < 9:
+                continue
+            try:
+                rows.append([x.strip() for x in r])
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        load = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_sha(relpath):
+    with open(os.path.join(ROOT, relpath), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_file, tag):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = source_sha(kernel_file)
+    for line in open(path):
+        parts = line.split()
+        # "<kernel>:<precision> <dram bytes per launch> <source sha256[:16]>"
+        if len(parts) >= 3 and parts[0] == tag and parts[2] == sha:
+            return float(parts[1])
+    return None
+
+
+# --------------------------------------------------------------------------- main arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads
+    import paper_2607_00488_gb300 as srw
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    P = args.points
+    wl = workloads.batched_scan_workload(P, theta_seed=3 + rank)
+    counts = workloads.load_counts(WORKLOAD_DATA)
+    lk = srw.Likelihood(wl, counts)
+    h = lk.handle
+    info = lk.info()
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = "bf16x3" if info["tensor_path"] else "fp32"
+    prec = srw.PRECISIONS[prec_name]
+    if prec != srw.SRW_FP32:
+        srw.srw_autotune(h, P, prec)
+
+    stream = torch.cuda.current_stream(dev)
+    th = torch.tensor(wl["theta"], device=dev)
+    out = torch.empty(P, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    srw.srw_profile(h, True)
+    for _ in range(args.warmup):
+        flush.add_(1.0)
+        lk.loglik(th, prec, out=out, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, fold_ms = [], []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        lk.loglik(th, prec, out=out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        fold_ms.append(srw.srw_profile_read(h))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * P / (total_ms * 1e-3)
+    srw.srw_profile(h, False)
+
+    # roofline of the fold kernel (useful flops 2 N_rec N_T per point)
+    peaks, peak_src = measured_peaks()
+    fold_avg_s = statistics.mean(fold_ms) * 1e-3
+    useful = 2.0 * info["n_rec"] * info["n_t"] * P
+    if prec == srw.SRW_FP32:
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, kernel_file, tag = "alu", "paper_2607_00488_gb300/csrc/fold_simt.cu", "fold_simt_kernel"
+    else:
+        peak = peaks["bf16_tflops"]
+        bound, kernel_file, tag = "tensor", "paper_2607_00488_gb300/csrc/fold_tc.cu", "fold_tc_kernel"
+    achieved = useful / fold_avg_s / 1e12
+    executed = useful * (3 if prec == srw.SRW_BF16X3 else 1)
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(kernel_file, tag + ":" + prec_name),
+                "kernel": tag, "peak_source": ("%s (%s)" % (peak_src, "bf16 burst" if bound == "tensor" else
+                                                           "FP32 FMA lanes x max clock")),
+                "executed_tflops": executed / fold_avg_s / 1e12, "fold_ms": statistics.mean(fold_ms)}
+
+    # e2e: the public call with host buffers (H2D theta, D2H result inside the timing)
+    th_host = np.ascontiguousarray(wl["theta"])
+    lk.loglik(th_host, prec)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lk.loglik(th_host, prec)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": P / statistics.mean(e2e_t), "unit": UNIT, "h2d_bytes_per_step": th_host.nbytes,
+           "d2h_bytes_per_step": P * 8}
+
+    # the plain single-point FP32 path (the 50x denominator): one call per point, L2 flushed
+    single = {}
+    th1 = torch.tensor(wl["theta"][:1], device=dev)
+    o1 = torch.empty(1, dtype=torch.float64, device=dev)
+    lk.loglik(th1, srw.SRW_FP32, out=o1, stream=stream)
+    ms1 = []
+    for k in range(50):
+        flush.add_(1.0)
+        th1.copy_(th[k:k + 1])
+        e0.record(stream)
+        lk.loglik(th1, srw.SRW_FP32, out=o1, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms1.append(e0.elapsed_time(e1))
+    single["cold_l2_evals_s"] = 1e3 / statistics.mean(ms1)
+    thb = th[:256].contiguous()
+    ob = torch.empty(256, dtype=torch.float64, device=dev)
+    lk.loglik_points(thb, out=ob, stream=stream)
+    e0.record(stream)
+    lk.loglik_points(thb, out=ob, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    single["warm_l2_evals_s"] = 256e3 / e0.elapsed_time(e1)
+    single["batched_over_single_cold"] = value / world / single["cold_l2_evals_s"]
+    gpu_vals = out.cpu().numpy()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if prec != srw.SRW_FP32 else "f32", "data": "synthetic",
+        "config": workload_config(P, prec_name), "roofline": roofline, "e2e": e2e,
+        "gpu_launches": 2 * args.steps, "single_point_fp32": single,
+    }
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        idx, vals, dt = oracle_subprocess(P, args.cpu_sample, 3)
+        d = [abs(gpu_vals[i] - v) for i, v in zip(idx, vals)]
+        line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%d evenly spaced theta of the %d-point batch, FP64 numpy, 1 thread"
+                                          % (len(idx), P)}
+        line["parity_sample"] = {"n": len(d), "max_abs_d": max(d), "median_abs_d": statistics.median(d)}
+    if rank == 0:
+        print(json.dumps(line))
+    lk.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * srw.h - spectrum-reweighting likelihood for solar neutrino-electron
+ * scattering on NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Implements the per-parameter-point likelihood of arXiv 2607.00488 ("GPU-
+ * accelerated spectrum reweighting for new-physics searches in solar
+ * neutrino-electron scattering"):
+ *   (a) recoil spectrum S_i(theta) per true-recoil bin from the flavour-
+ *       weighted nu-e cross section (Sec. II, eqs. sm_cross_section,
+ *       g_tilde, xs_mm, xs_total; Sec. III.A eq. fT) and the bin weights
+ *       w_i = S_i(theta)/S_i(SM) (eqs. fT_norm, reweight_factor);
+ *   (b) the fold through a fixed response R (eq. matrix_reweight,
+ *       eq. visible_spectrum, eq. fNp_reweight);
+ *   (c) the Poisson -2 ln L against binned data plus background templates
+ *       (eqs. mu_total, logL; the Gaussian pull terms stay with the caller,
+ *       as in Sec. IV.B).
+ *
+ * Parameter point layout (float32, 5 per point):
+ *   theta = { eps_L_ee, eps_R_ee, eps_L_tautau, eps_R_tautau, mu_hat }
+ *   with mu_hat = mu_nu / (1e-11 Bohr magnetons).  The NSI couplings shift
+ *   the chiral couplings g_{L,R} of nu_e and nu_tau (eq. g_tilde); nu_mu
+ *   keeps its SM couplings.
+ *
+ * Conventions
+ *   - Energies are in MeV.  Cross sections are in units of
+ *     sigma0 = 2 G_F^2 m_e / pi; the absolute scale cancels in the weights.
+ *   - Every input array is COPIED by the library during the call that takes
+ *     it; the caller keeps ownership and may free it on return.
+ *   - Output buffers are owned by the caller.
+ *   - `where` = SRW_HOST: pointers are host memory and the call returns when
+ *     the result is in host memory.  `where` = SRW_DEVICE: pointers are
+ *     device memory on the handle's device, and the call is asynchronous,
+ *     stream-ordered on `stream` (a cudaStream_t; NULL = a stream owned by
+ *     the handle, synchronised before return).
+ *   - No C++ exception crosses this boundary.  Every call returns a status;
+ *     srw_last_error() gives a message for the last failure on a handle.
+ *   - A handle is not thread-safe: use one host thread (and one stream) per
+ *     handle at a time.
+ *   - All hot-path work runs in the library's CUDA kernels.  If no CUDA
+ *     device is usable, srw_create fails with SRW_ECUDA; there is no CPU
+ *     fallback.
+ */
+#ifndef SRW_H_
+#define SRW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srw_ctx* srw_handle;
+
+typedef enum {
+  SRW_OK = 0,
+  SRW_EINVAL = 1,       /* invalid argument: null pointer, size, NaN, unsorted edges */
+  SRW_ENOMEM = 2,       /* device or host allocation failed */
+  SRW_ECUDA = 3,        /* a CUDA runtime/driver call failed (message in srw_last_error) */
+  SRW_ENODATA = 4,      /* srw_loglik before srw_set_data */
+  SRW_EDOMAIN = 5,      /* some mu_j <= 0 with n_j > 0 (or mu_j < 0): that point's -2lnL is +inf */
+  SRW_ETIMEOUT = 6,     /* a bounded device-side wait expired; the kernel aborted cleanly */
+  SRW_EUNSUPPORTED = 7  /* the device cannot run the requested path (needs sm_103) */
+} srw_status;
+
+typedef enum { SRW_HOST = 0, SRW_DEVICE = 1 } srw_where;
+
+/* Arithmetic of the response fold in the batched path.
+ *   SRW_FP32   : FP32 SIMT products, FP32 accumulation with compensated
+ *                chunk sums.
+ *   SRW_BF16   : R and the weighted spectra rounded to BF16 on the tcgen05
+ *                tensor cores, FP32 accumulation in tensor memory.
+ *   SRW_BF16X3 : both operands split x = hi + lo (BF16 each, round to
+ *                nearest even); the three products hi*hi + hi*lo + lo*hi
+ *                accumulate in FP32 on the tensor cores.
+ * The -2lnL bin reduction accumulates in FP64 for every precision. */
+typedef enum { SRW_FP32 = 0, SRW_BF16 = 1, SRW_BF16X3 = 2 } srw_precision;
+
+/* Recoil binning (Sec. III.A).  The lower integration limit of every bin is
+ * max(T_lo, t_min): t_min > 0 is the analysis threshold that regulates the
+ * 1/T magnetic-moment term (Sec. II.C).  midpoint = 0 integrates the cross
+ * section over each bin in closed form (default); midpoint = 1 evaluates it at
+ * the bin centre times the bin width (eq. fT literally; a bin counts for a
+ * node iff t_min <= T_c < T_max(E)). */
+typedef struct {
+  int n_t;                /* number of true-recoil bins, >= 1 */
+  const double* t_edges;  /* n_t + 1 strictly ascending edges, t_edges[0] >= 0, MeV */
+  int n_rec;              /* number of reconstructed bins, >= 1 */
+  double t_min;           /* threshold, MeV, > 0 (1e-3 if <= 0 is passed) */
+  int midpoint;           /* 0 = bin-integrated (default), 1 = midpoint */
+} srw_binning;
+
+/* One solar-neutrino component k (Sec. II.A, eq. rate_sm; Sec. III.A,
+ * eq. fT): energy nodes E_n with weights w_n = phi_k(E_n) dE_n (a line is a
+ * single node) and survival probability P_ee(E_n).  The nu_mu / nu_tau split
+ * of 1 - P_ee is (1 - f_tau, f_tau). */
+typedef struct {
+  int n_nodes;            /* >= 1 */
+  const double* e;        /* n_nodes neutrino energies, MeV, > 0 */
+  const double* w;        /* n_nodes weights, >= 0, arbitrary units */
+  const double* pee;      /* n_nodes survival probabilities in [0, 1] */
+} srw_source;
+
+typedef struct {
+  double sin2w;           /* weak mixing angle sin^2(theta_W); <= 0 selects 0.23121 */
+  double f_tau;           /* nu_tau fraction of 1 - P_ee; < 0 selects 0.5 */
+  double exposure;        /* expected signal events after the response at theta = 0 (> 0) */
+  const double* e_true_sm;/* optional n_t baseline true-recoil SM histogram (the MC
+                             baseline E_true^SM of eq. matrix_reweight); NULL: use
+                             lambda * S_SM with sum_j (R E_SM)_j = exposure */
+} srw_options;
+
+/* Create a likelihood context on the current CUDA device.
+ *   R: n_rec x n_t row-major float32, host memory: the conditional response
+ *      R[j][i] = P(reconstructed bin j | true bin i) (eq. visible_spectrum;
+ *      column sums are the efficiency).  Must be finite and >= 0.
+ * Builds, on the device, the FP64 coefficient spectra of the recoil spectrum
+ * (the spectrum is a polynomial in the couplings and mu_hat^2), the SM
+ * spectrum, the baseline E_SM, and the BF16 hi/lo split of R.
+ * Errors: SRW_EINVAL (bad sizes/values), SRW_ENOMEM, SRW_ECUDA. */
+srw_status srw_create(const srw_binning* binning, const srw_source* sources, int n_sources,
+                      const float* R, const srw_options* options, srw_handle* out);
+
+/* Attach binned data (eqs. mu_total, logL).  Host pointers:
+ *   counts: n_rec observed counts n_j >= 0 (need not be integers);
+ *   bkg:    n_bkg x n_rec background templates in expected counts (summed);
+ *           may be NULL when n_bkg == 0;
+ *   mask:   n_rec live-bin mask M_j (0 drops the bin), or NULL for all bins.
+ * Precomputes the theta-independent part of -2lnL in FP64 on the device. */
+srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, int n_bkg,
+                        const unsigned char* mask);
+
+/* Spectra at one parameter point theta (5 floats, host or device per `where`).
+ *   stage 0: S_i(theta), the recoil spectrum per true bin        (n_t floats)
+ *   stage 1: W_i = w_i(theta) E_SM,i, the reweighted true spectrum (n_t floats)
+ *   stage 2: sum_i R_ji W_i, the folded signal                   (n_rec floats)
+ *   stage 3: mu_j = M_j (signal_j + background_j)                (n_rec floats)
+ * Computed by the single-point kernels (FP32). */
+srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out, int where, void* stream);
+
+/* -2 ln L (without pull terms) for P parameter points.
+ *   theta: P x 5 float32; out: P float64.
+ * P == 1 with SRW_FP32 runs the single-point path (spectrum kernel, HBM-
+ * streaming fold, fused Poisson reduction); otherwise the batched path (one
+ * persistent fold launch over all points with the Poisson reduction fused
+ * into its epilogue) in the requested precision.  Each distinct
+ * (path, precision, P, theta, out, stream) call signature is captured once
+ * into a CUDA graph and replayed.
+ * Returns SRW_EDOMAIN (host calls only) when a point's value is +inf. */
+srw_status srw_loglik(srw_handle h, const float* theta, int P, double* out, int where,
+                      srw_precision precision, void* stream);
+
+/* The plain single-point FP32 path applied to P points one after another:
+ * per point one spectrum launch and one fold launch, in order (replayed from
+ * a captured CUDA graph per call signature, like srw_loglik). */
+srw_status srw_loglik_points(srw_handle h, const float* theta, int P, double* out, int where, void* stream);
+
+/* Folded signal spectra for P points with the batched fold:
+ *   out[p * n_rec + j] = sum_i R_ji W_i(theta_p)   (P x n_rec float32)
+ * in the requested precision (eq. matrix_reweight for a batch of points; no
+ * data needed).  This is the exact-path generator of training spectra for a
+ * learned surrogate.  Host calls allocate a temporary device buffer. */
+srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* out, int where,
+                              srw_precision precision, void* stream);
+
+/* Copy the eight FP64 coefficient spectra B[8][n_t] (host memory) such that
+ * S(theta) = sum_b c_b(theta) B_b with
+ *   c = { gLe^2, gRe^2, -gLe gRe, gLt^2, gRt^2, -gLt gRt, 1, mu_hat^2 }
+ * (e = nu_e, t = nu_tau couplings after the NSI shift; index 6 is the full
+ * nu_mu spectrum; index 7 the magnetic-moment spectrum for mu_hat = 1). */
+srw_status srw_get_basis(srw_handle h, double* out);
+
+/* Time the candidate tile configurations of the batched fold for P points
+ * at `precision` and keep the fastest for this handle.  If `cache_path` is
+ * not NULL the choice is also read from / appended to that text file.
+ * `chosen` (may be NULL) receives the index of the chosen configuration. */
+srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char* cache_path,
+                        void* stream, int* chosen);
+
+/* Sizes of a context. */
+typedef struct {
+  int n_t, n_rec, n_nodes, k_pad;
+  int device, sm_count, tensor_path;   /* tensor_path: 1 if the tcgen05 fold can run */
+  double lambda;                        /* E_SM = lambda * S_SM normalisation (0 if e_true_sm given) */
+  size_t device_bytes;                  /* persistent device memory held by the context */
+} srw_info_t;
+srw_status srw_info(srw_handle h, srw_info_t* info);
+
+/* Reference point of the folds.  Every fold is evaluated as
+ *   mu(theta) = R W_ref + R (W(theta) - W_ref)
+ * (the same quantity as R W(theta), eq. matrix_reweight), with R W_ref
+ * computed once in FP64, so the rounding errors of the FP32 and BF16 folds
+ * scale with |W(theta) - W_ref| instead of |W(theta)|.  The default
+ * reference is the SM point theta = 0.  theta_ref (5 floats, host memory)
+ * selects another point (e.g. the current best fit); NULL disables the
+ * reference (mu = R W(theta) folded directly in the chosen precision).
+ * Synchronous; invalidates captured graphs. */
+srw_status srw_set_reference(srw_handle h, const float* theta_ref);
+
+/* Kernel timing.  With profiling enabled, srw_loglik records CUDA events
+ * immediately before and after its fold launch (the GEMV of the single-point
+ * path, the batched fold otherwise); srw_profile_read waits for the last such
+ * launch and returns its device time in milliseconds.  Enabling or disabling
+ * profiling selects a different captured graph. */
+srw_status srw_profile(srw_handle h, int enable);
+srw_status srw_profile_read(srw_handle h, float* fold_ms);
+
+const char* srw_last_error(srw_handle h);
+const char* srw_status_string(srw_status s);
+srw_status srw_destroy(srw_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRW_H_ */

@@ -1,0 +1,199 @@
+// Batched fold in FP32 on the SIMT pipes (the FP32 way of the batched scan).
+//
+// For P parameter points the fold of eq. matrix_reweight becomes the
+// contraction  M[p][j] = sum_i W[p][i] R[j][i]  with the reweighted true
+// spectra W[p][i] = w_i(theta_p) E_SM,i.  Because the recoil spectrum is a
+// polynomial in the couplings, W[p][i] = sum_b c_b(theta_p) shat_b,i with the
+// eight pre-weighted coefficient spectra shat (built once in FP64); each
+// block produces its W tile on chip from shat and the 8 coefficients of its
+// points, so W is never written to memory.  The epilogue adds the summed
+// background, applies the mask, evaluates the Poisson terms and reduces over
+// its rec bins per point into FP64 partials (one per rec tile).  The fold is
+// taken of W(theta) - W_ref; the FP64 reference fold R W_ref enters with the
+// background (b64 argument = background + reference fold).
+//
+// Accumulation: FP32 FMAs over 64-wide K chunks, chunks combined with
+// Kahan compensation, so the FP32 rounding of long rows stays ~1e-8.
+
+#include "dfloat.cuh"
+#include "poisson.cuh"
+#include "srw_internal.h"
+
+namespace srw {
+namespace {
+
+constexpr int BM = 64;    // points per block
+constexpr int BN = 128;   // rec bins per block
+constexpr int BK = 16;
+constexpr int THR = 256;  // 16 x 16 threads
+constexpr int TM = 4;     // points per thread
+constexpr int TN = 8;     // rec bins per thread
+constexpr int CHUNK = 4;  // K tiles per compensated chunk
+
+// Coupling monomials c_b(theta) (see srw_internal.h) in double-float
+// arithmetic, returned as hi + lo float pairs so that W carries no per-theta
+// rounding bias.
+__device__ __forceinline__ void coefficients(const float* th, dfloat s, const CoefRef& ref, float* hi, float* lo) {
+  const dfloat gle = df_add(df_add(dfloat{0.5f, 0.f}, s), th[0]), gre = df_add(s, th[1]);
+  const dfloat glt = df_add(df_add(dfloat{-0.5f, 0.f}, s), th[2]), grt = df_add(s, th[3]);
+  const dfloat x = df_mul(gle, gre), y = df_mul(glt, grt);
+  const dfloat c[kNB] = {df_mul(gle, gle), df_mul(gre, gre), {-x.hi, -x.lo}, df_mul(glt, glt),
+                         df_mul(grt, grt), {-y.hi, -y.lo}, {1.f, 0.f}, two_prod(th[4], th[4])};
+#pragma unroll
+  for (int b = 0; b < kNB; ++b) {
+    const dfloat d = df_add(c[b], dfloat{-ref.hi[b], -ref.lo[b]});  // deviation from the reference point
+    hi[b] = d.hi;
+    lo[b] = d.lo;
+  }
+}
+
+__global__ void __launch_bounds__(THR)
+fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef cref, const float* __restrict__ shat,
+                 const float* __restrict__ shat_lo, int k_pad, const float* __restrict__ R, int n_rec, int ld,
+                 const double* __restrict__ n64, const double* __restrict__ b64,
+                 const unsigned char* __restrict__ mask, double* __restrict__ parts,
+                 float* __restrict__ musig_out) {
+  __shared__ float cs[BM][2 * kNB + 1];
+  __shared__ __align__(16) float Ws[BK][BM];
+  __shared__ __align__(16) float Rs[BK][BN + 4];
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+
+  if (tid < BM) {
+    float hi[kNB], lo[kNB];
+    const int p = m0 + tid;
+    if (p < P) {
+      coefficients(theta + (size_t)p * 5, sin2w, cref, hi, lo);
+    } else {
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) hi[b] = lo[b] = 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < kNB; ++b) {
+      cs[tid][b] = hi[b];
+      cs[tid][kNB + b] = lo[b];
+    }
+  }
+
+  float acc[TM][TN], sum[TM][TN], comp[TM][TN];
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[r][c] = sum[r][c] = comp[r][c] = 0.f;
+
+  const int n_kt = k_pad / BK;
+  for (int kt = 0; kt < n_kt; ++kt) {
+    const int k0 = kt * BK;
+    __syncthreads();
+    {  // produce W^T tile: W[p][k] = sum_b c_b(p) shat_b[k]
+      const int k = tid & (BK - 1), mg = (tid >> 4) * TM;
+      float sh[kNB], sl[kNB];
+#pragma unroll
+      for (int b = 0; b < kNB; ++b) {
+        sh[b] = __ldg(shat + (size_t)b * k_pad + k0 + k);
+        sl[b] = __ldg(shat_lo + (size_t)b * k_pad + k0 + k);
+      }
+      float v[TM];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) {
+        // (c_hi + c_lo)(s_hi + s_lo) without the lo*lo term
+        float s = 0.f, t = 0.f;
+#pragma unroll
+        for (int b = 0; b < kNB; ++b) {
+          s = fmaf(cs[mg + r][b], sh[b], s);
+          t = fmaf(cs[mg + r][kNB + b], sh[b], fmaf(cs[mg + r][b], sl[b], t));
+        }
+        v[r] = s + t;
+      }
+      *reinterpret_cast<float4*>(&Ws[k][mg]) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {  // R tile, transposed into Rs[k][j]
+      const int f = tid + rr * THR, row = f >> 2, c4 = f & 3;
+      const int j = j0 + row;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < n_rec) v = __ldg(reinterpret_cast<const float4*>(R + (size_t)j * ld + k0 + c4 * 4));
+      Rs[c4 * 4 + 0][row] = v.x;
+      Rs[c4 * 4 + 1][row] = v.y;
+      Rs[c4 * 4 + 2][row] = v.z;
+      Rs[c4 * 4 + 3][row] = v.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&Ws[k][ty * TM]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Rs[k][tx * TN]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Rs[k][tx * TN + 4]);
+      const float av[TM] = {a.x, a.y, a.z, a.w};
+      const float bv[TN] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    }
+    if ((kt + 1) % CHUNK == 0 || kt + 1 == n_kt) {
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+          const float y = acc[r][c] - comp[r][c];
+          const float t = sum[r][c] + y;
+          comp[r][c] = (t - sum[r][c]) - y;
+          sum[r][c] = t;
+          acc[r][c] = 0.f;
+        }
+    }
+  }
+
+  if (musig_out != nullptr) {  // batched folded spectra
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+      const int p = m0 + ty * TM + r;
+      if (p >= P) continue;
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const int j = j0 + tx * TN + c;
+        if (j < n_rec) musig_out[(size_t)p * n_rec + j] = sum[r][c] - comp[r][c];
+      }
+    }
+  }
+  if (parts == nullptr) return;
+  // Epilogue: Poisson terms (FP64) over this block's rec bins, per point.
+  double nj[TN], bj[TN];
+  bool on[TN];
+#pragma unroll
+  for (int c = 0; c < TN; ++c) {
+    const int j = j0 + tx * TN + c;
+    on[c] = j < n_rec && (mask == nullptr || mask[j] != 0);
+    nj[c] = on[c] ? n64[j] : 0.0;
+    bj[c] = on[c] ? b64[j] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < TM; ++r) {
+    double d = 0.0;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      if (on[c]) d += poisson_term_f64(((double)sum[r][c] - (double)comp[r][c]) + bj[c], nj[c]);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const int p = m0 + ty * TM + r;
+    if (tx == 0 && p < P) parts[(size_t)blockIdx.y * P + p] = d;
+  }
+}
+
+}  // namespace
+
+int fold_simt_parts(int n_rec) { return (n_rec + BN - 1) / BN; }
+
+cudaError_t launch_fold_simt(const srw_ctx* h, const float* theta, int P, double* parts, cudaStream_t s,
+                             int* n_parts, float* musig_out) {
+  const dim3 grid((P + BM - 1) / BM, (h->n_rec + BN - 1) / BN);
+  fold_simt_kernel<<<grid, THR, 0, s>>>(theta, P, df_from_double(h->sin2w), h->cref, h->d_shat, h->d_shat_lo, h->k_pad, h->d_R, h->n_rec,
+                                        h->ld_r, h->d_n64, h->d_bref64, h->d_mask, parts, musig_out);
+  if (n_parts) *n_parts = (int)grid.y;
+  return cudaGetLastError();
+}
+
+}  // namespace srw

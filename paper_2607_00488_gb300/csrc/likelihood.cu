@@ -1,0 +1,310 @@
+// Single-point fold + Poisson reduction, data set-up and partial-sum reduction.
+//
+// Fold (eq. visible_spectrum / eq. matrix_reweight):
+//   mu_sig_j = sum_i R_ji W_i,  W_i = w_i(theta) E_SM,i
+// Expectation (eq. mu_total) and -2 ln L (eq. logL):
+//   mu_j = M_j (mu_sig_j + b_j),  -2lnL = C + 2 sum_j t(mu_j, n_j)
+//
+// The single-point fold is a GEMV bound by HBM bandwidth: R (n_rec x k_pad
+// FP32) is read exactly once.  It is streamed into shared memory by the TMA
+// engine (bulk async copies completing on mbarriers), so the number of bytes
+// in flight per SM is set by the ring depth rather than by registers.  The
+// Poisson term and the bin reduction are FP64 and fused into the same launch
+// (the last block to finish sums the per-block partials in block order).
+
+#include "dfloat.cuh"
+#include "poisson.cuh"
+#include "ptx.cuh"
+#include "srw_internal.h"
+
+namespace srw {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// One block per SM owns a contiguous range of rows.  A producer warp streams
+// R in chunks of up to 16 KB into a kGvStages-deep ring; eight consumer warps
+// each take one eighth of every chunk, multiply by W (read through L1), keep
+// FP32 partial sums per chunk and fold them into an FP64 per-lane
+// accumulator.  A consumer warp releases a stage with one arrive.  Every wait
+// is bounded (see ptx.cuh); a block that gives up raises kStatusTimeout.
+// ---------------------------------------------------------------------------
+constexpr int kGvConsumers = 8;
+constexpr int kGvThreads = (kGvConsumers + 1) * 32;
+constexpr int kGvChunk = 4096;  // floats per stage (16 KB)
+constexpr int kGvStages = 6;
+
+__global__ void __launch_bounds__(kGvThreads, 1)
+fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_block, const float* __restrict__ W,
+                  const double* __restrict__ muref, const double* __restrict__ n64, const double* __restrict__ b64,
+                  const unsigned char* __restrict__ mask, const double* __restrict__ c_data,
+                  float* __restrict__ musig_out, float* __restrict__ mu_out, double* __restrict__ parts,
+                  unsigned* __restrict__ ticket, double* __restrict__ out, unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char dsmem[];
+  const int chunk = ld < kGvChunk ? ld : kGvChunk;
+  float* sbuf = reinterpret_cast<float*>(dsmem);
+  float2* spart = reinterpret_cast<float2*>(dsmem + sizeof(float) * (size_t)kGvStages * chunk);
+  __shared__ __align__(8) uint64_t full[kGvStages], empty[kGvStages];
+  __shared__ unsigned abort_flag;
+  __shared__ double sred[kGvThreads / 32];
+  __shared__ bool is_last;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(n_rec, r0 + rows_per_block);
+  const int nrows = r1 > r0 ? r1 - r0 : 0;
+  const int cpr = (ld + chunk - 1) / chunk;  // chunks per row
+  const int n_units = nrows * cpr;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kGvStages; ++st) {
+      ptx::mbar_init(&full[st], 1);
+      ptx::mbar_init(&empty[st], kGvConsumers);
+    }
+    abort_flag = 0u;
+    ptx::fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == kGvConsumers) {
+    // ---- producer (one lane)
+    if (lane == 0) {
+      int issued = 0;
+      for (int u = 0; u < n_units; ++u) {
+        const int st = u % kGvStages;
+        if (u >= kGvStages && !ptx::mbar_wait(&empty[st], ((u / kGvStages) - 1) & 1, &abort_flag)) {
+          atomicExch(&abort_flag, 1u);
+          atomicOr(status, kStatusTimeout);
+          break;
+        }
+        const int row = r0 + u / cpr, k0 = (u % cpr) * chunk;
+        const int len = min(chunk, ld - k0);
+        ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)len * 4u);
+        ptx::bulk_g2s(sbuf + (size_t)st * chunk, R + (size_t)row * ld + k0, (uint32_t)len * 4u, &full[st]);
+        issued = u + 1;
+      }
+      // never let the block end with copies in flight
+      for (int u = max(0, issued - kGvStages); u < issued; ++u)
+        ptx::mbar_wait(&full[u % kGvStages], (u / kGvStages) & 1, nullptr, 100000000ull);
+    }
+  } else {
+    // ---- consumers (no FP64 here: the chunk sums accumulate as double-floats)
+    dfloat lacc = {0.f, 0.f};
+    for (int u = 0; u < n_units; ++u) {
+      const int st = u % kGvStages;
+      if (!ptx::mbar_wait(&full[st], (u / kGvStages) & 1, &abort_flag)) {
+        if (lane == 0) {
+          atomicExch(&abort_flag, 1u);
+          atomicOr(status, kStatusTimeout);
+        }
+        break;
+      }
+      const int c = u % cpr, k0 = c * chunk;
+      const int len = min(chunk, ld - k0), slice = len / kGvConsumers;  // a multiple of 8 floats
+      const float4* buf = reinterpret_cast<const float4*>(sbuf + (size_t)st * chunk + warp * slice);
+      const float4* w4 = reinterpret_cast<const float4*>(W + k0 + warp * slice);
+      float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+      for (int q = lane; q < slice / 4; q += 32) {
+        const float4 r = buf[q];
+        const float4 w = __ldg(w4 + q);
+        ax = fmaf(r.x, w.x, ax);
+        ay = fmaf(r.y, w.y, ay);
+        az = fmaf(r.z, w.z, az);
+        aw = fmaf(r.w, w.w, aw);
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[st]);
+      lacc = df_add(lacc, (ax + ay) + (az + aw));
+      if (c == cpr - 1) {
+        const dfloat v = df_warp_sum(lacc);
+        if (lane == 0) spart[(u / cpr) * kGvConsumers + warp] = make_float2(v.hi, v.lo);
+        lacc = {0.f, 0.f};
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- epilogue: mu_j, FP64 Poisson terms, block partial
+  double t = 0.0;
+  if (abort_flag == 0u) {
+    for (int rl = threadIdx.x; rl < nrows; rl += kGvThreads) {
+      const int j = r0 + rl;
+      dfloat ms = {0.f, 0.f};
+      for (int w = 0; w < kGvConsumers; ++w) {
+        const float2 v = spart[rl * kGvConsumers + w];
+        ms = df_add(ms, dfloat{v.x, v.y});
+      }
+      // delta mode: W holds W(theta) - W_ref, and the FP64 reference fold is added back
+      const double musig = (double)ms.hi + (double)ms.lo + (muref != nullptr ? muref[j] : 0.0);
+      const bool on = mask == nullptr || mask[j] != 0;
+      const double mu = on ? musig + (b64 != nullptr ? b64[j] : 0.0) : 0.0;
+      if (musig_out) musig_out[j] = (float)musig;
+      if (mu_out) mu_out[j] = (float)mu;
+      if (on && out) {
+        const double tj = poisson_term_f64(mu, n64[j]);
+        if (isinf(tj)) atomicOr(status, kStatusDomain);
+        t += tj;
+      }
+    }
+  }
+  if (out == nullptr) return;
+  t = warp_sum_d(t);
+  if (lane == 0) sred[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kGvThreads / 32; ++w) s += sred[w];
+    parts[blockIdx.x] = s;
+    __threadfence();
+    const unsigned prev = atomicAdd(ticket, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  // last block: fixed-order FP64 sum of all partials
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kGvThreads) s += ((volatile double*)parts)[b];
+  s = warp_sum_d(s);
+  __syncthreads();
+  if (lane == 0) sred[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < kGvThreads / 32; ++w) tot += sred[w];
+    out[0] = 2.0 * tot + *c_data;
+    *ticket = 0u;
+  }
+}
+
+// out[p] = 2 sum_t parts[t][p] + C  (fixed order over t).
+__global__ void reduce_parts_kernel(const double* __restrict__ parts, int n_parts, int P,
+                                    const double* __restrict__ c_data, double* __restrict__ out,
+                                    unsigned* __restrict__ status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double s = 0.0;
+  for (int t = 0; t < n_parts; ++t) s += parts[(size_t)t * P + p];
+  const double v = 2.0 * s + *c_data;
+  if (isinf(v)) atomicOr(status, kStatusDomain);
+  out[p] = v;
+}
+
+// --- data set-up --------------------------------------------------------------
+__global__ void data_prepare_kernel(const double* __restrict__ bkg, int n_bkg, int n_rec,
+                                    double* __restrict__ b64) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_rec) return;
+  double b = 0.0;
+  for (int k = 0; k < n_bkg; ++k) b += bkg[(size_t)k * n_rec + j];
+  b64[j] = b;
+}
+
+// Per-bin constants of the batched epilogues: reference fold + background,
+// in FP64 (SIMT fold) and as floats with the count and the mask (tensor fold).
+__global__ void data_ref_kernel(const double* __restrict__ n64, const double* __restrict__ b64,
+                                const double* __restrict__ muref, const unsigned char* __restrict__ mask, int n_rec,
+                                double* __restrict__ bref64, float4* __restrict__ nbm, float2* __restrict__ nb2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_rec) return;
+  const double br = b64[j] + muref[j];
+  bref64[j] = br;
+  const bool on = mask == nullptr || mask[j] != 0;
+  nbm[j] = make_float4((float)n64[j], (float)br, on ? 1.f : 0.f, 0.f);
+  nb2[j] = make_float2(on ? (float)n64[j] : -1.f, (float)br);
+}
+
+// C = 2 sum_j M_j [n_j - n_j ln n_j + lnGamma(n_j + 1)], one block.
+__global__ void cdata_kernel(const double* __restrict__ n64, const unsigned char* __restrict__ mask, int n_rec,
+                             double* __restrict__ c_out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n_rec; j += blockDim.x) {
+    if (mask != nullptr && mask[j] == 0) continue;
+    const double n = n64[j];
+    const double nlogn = n > 0.0 ? n * log(n) : 0.0;
+    s += n - nlogn + lgamma(n + 1.0);
+  }
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *c_out = 2.0 * t;
+  }
+}
+
+}  // namespace
+
+static int gv_rows_per_block(const srw_ctx* h) {
+  const int g = h->sm_count > 0 ? h->sm_count : 148;
+  return (h->n_rec + g - 1) / g;
+}
+
+int fold_point_grid(const srw_ctx* h) {
+  const int rpb = gv_rows_per_block(h);
+  return (h->n_rec + rpb - 1) / rpb;
+}
+
+static size_t gv_smem(const srw_ctx* h) {
+  const int chunk = h->ld_r < kGvChunk ? h->ld_r : kGvChunk;
+  return sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * (size_t)kGvConsumers * gv_rows_per_block(h);
+}
+
+void fold_point_init() {
+  cudaFuncSetAttribute(fold_point_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out, float* mu_out, double* out,
+                              cudaStream_t s, bool delta) {
+  const size_t smem = gv_smem(h);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const double* muref = (delta && h->use_ref) ? h->d_muref64 : nullptr;
+  fold_point_kernel<<<fold_point_grid(h), kGvThreads, smem, s>>>(
+      h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
+      mu_out, h->d_part, h->d_ticket, out, h->d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_parts(const srw_ctx* h, const double* parts, int n_parts, int P, double* out,
+                                cudaStream_t s) {
+  const int thr = 256;
+  reduce_parts_kernel<<<(P + thr - 1) / thr, thr, 0, s>>>(parts, n_parts, P, h->d_cdata, out, h->d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStream_t s) {
+  const int thr = 256;
+  data_prepare_kernel<<<(h->n_rec + thr - 1) / thr, thr, 0, s>>>(d_bkg, n_bkg, h->n_rec, h->d_b64);
+  cdata_kernel<<<1, 1024, 0, s>>>(h->d_n64, h->d_mask, h->n_rec, h->d_cdata);
+  return launch_data_ref(h, s);
+}
+
+cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s) {
+  const int thr = 256;
+  data_ref_kernel<<<(h->n_rec + thr - 1) / thr, thr, 0, s>>>(h->d_n64, h->d_b64, h->d_muref64, h->d_mask, h->n_rec,
+                                                             h->d_bref64, h->d_nbm, h->d_nb2);
+  return cudaGetLastError();
+}
+
+// out[p][j] += mu_ref[j]: folded spectra of the batched path from deviations.
+__global__ void add_ref_kernel(float* __restrict__ out, const double* __restrict__ muref, int P, int n_rec) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)P * n_rec) return;
+  out[idx] += (float)muref[idx % n_rec];
+}
+
+cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s) {
+  if (!h->use_ref) return cudaSuccess;
+  const size_t n = (size_t)P * h->n_rec;
+  add_ref_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, h->d_muref64, P, h->n_rec);
+  return cudaGetLastError();
+}
+
+}  // namespace srw

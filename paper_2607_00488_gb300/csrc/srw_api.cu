@@ -1,0 +1,844 @@
+// C-ABI entry points of the srw library: validation, device tables, dispatch
+// and the per-signature CUDA-graph cache.  See include/srw.h for the contract.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "srw_internal.h"
+
+namespace srw {
+
+
+static thread_local std::string g_create_err;
+
+srw_status fail(srw_ctx* h, srw_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return s;
+}
+
+srw_status cuda_fail(srw_ctx* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? SRW_ENOMEM : SRW_ECUDA, m);
+}
+
+ModelView model_view(const srw_ctx* h) {
+  ModelView m;
+  m.n_t = h->n_t;
+  m.n_rec = h->n_rec;
+  m.n_nodes = h->n_nodes;
+  m.k_pad = h->k_pad;
+  m.ld_r = h->ld_r;
+  m.midpoint = h->midpoint;
+  m.t_min = (float)h->t_min;
+  m.t_min64 = h->t_min;
+  m.node_a = h->d_node_a;
+  m.node_w = h->d_node_w;
+  m.node_c = h->d_node_c;
+  m.node_wlo = h->d_node_wlo;
+  m.node64 = h->d_node64;
+  m.bin_count = h->d_bin_count;
+  m.bin_f = h->d_bin_f;
+  m.bin_l = h->d_bin_l;
+  m.bin64 = h->d_bin64;
+  m.ssm32 = h->d_ssm32;
+  m.esm32 = h->d_esm32;
+  m.R = h->d_R;
+  return m;
+}
+
+DataView data_view(const srw_ctx* h) {
+  DataView d;
+  d.n_rec = h->n_rec;
+  d.n64 = h->d_n64;
+  d.b64 = h->d_b64;
+  d.nbm = h->d_nbm;
+  d.mask = h->d_mask;
+  d.c_data = h->d_cdata;
+  return d;
+}
+
+template <class T>
+static cudaError_t dalloc(srw_ctx* h, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1));
+  if (e == cudaSuccess) h->device_bytes += sizeof(T) * std::max<size_t>(n, 1);
+  return e;
+}
+
+template <class T>
+static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static float int_bits_as_float(int v) {
+  float f;
+  std::memcpy(&f, &v, sizeof f);
+  return f;
+}
+
+static void split_df(double x, float* hi, float* lo) {
+  *hi = (float)x;
+  *lo = (float)(x - (double)*hi);
+}
+
+// Monomials (batched folds) and coupling products (spectrum kernel) of the
+// reference point, in FP64 split into hi + lo floats; zeros when disabled.
+static void set_reference_coefs(srw_ctx* h) {
+  const double s = h->sin2w;
+  const double* t = nullptr;
+  double th[5];
+  for (int k = 0; k < 5; ++k) th[k] = (double)h->theta_ref[k];
+  t = th;
+  const double gle = 0.5 + s + t[0], gre = s + t[1], glt = -0.5 + s + t[2], grt = s + t[3];
+  const double glm = -0.5 + s, grm = s, mu2 = t[4] * t[4];
+  const double c[kNB] = {gle * gle, gre * gre, -gle * gre, glt * glt, grt * grt, -glt * grt, 1.0, mu2};
+  const double g[10] = {gle * gle, glm * glm, glt * glt, gre * gre, grm * grm, grt * grt,
+                        gle * gre, glm * grm, glt * grt, h->kappa * mu2};
+  for (int b = 0; b < kNB; ++b) {
+    if (h->use_ref) split_df(c[b], &h->cref.hi[b], &h->cref.lo[b]);
+    else h->cref.hi[b] = h->cref.lo[b] = 0.f;
+  }
+  for (int k = 0; k < 10; ++k) {
+    if (h->use_ref) split_df(g[k], &h->gref[0][k], &h->gref[1][k]);
+    else h->gref[0][k] = h->gref[1][k] = 0.f;
+  }
+}
+
+static bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+static void destroy_graphs(srw_ctx* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+static void release(srw_ctx* h) {
+  destroy_graphs(h);
+  tc_release(h);
+  dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_shat_lo); dfree(h->d_shat_k8); dfree(h->d_node64); dfree(h->d_bin_count); dfree(h->d_bin_f);
+  dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis); dfree(h->d_ssm64); dfree(h->d_esm64);
+  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo);
+  dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_mask); dfree(h->d_cdata);
+  dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
+  dfree(h->d_status); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  h->own_stream = nullptr;
+  for (auto& ev : h->ev_fold)
+    if (ev) cudaEventDestroy(ev);
+  h->ev_fold[0] = h->ev_fold[1] = nullptr;
+}
+
+#define SRW_CUDA(h, call, what)                      \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+static cudaStream_t pick_stream(srw_ctx* h, void* stream) {
+  return stream ? (cudaStream_t)stream : h->own_stream;
+}
+
+// Grows the staging buffers for host-pointer calls; invalidates graphs that
+// referenced the old buffers.
+static srw_status ensure_staging(srw_ctx* h, int P) {
+  if (P <= h->stage_cap) return SRW_OK;
+  int cap = std::max(P, 2 * h->stage_cap);
+  destroy_graphs(h);
+  dfree(h->d_theta);
+  dfree(h->d_out);
+  SRW_CUDA(h, cudaMalloc(&h->d_theta, sizeof(float) * 5 * (size_t)cap), "staging theta");
+  SRW_CUDA(h, cudaMalloc(&h->d_out, sizeof(double) * (size_t)cap), "staging out");
+  h->stage_cap = cap;
+  return SRW_OK;
+}
+
+static srw_status ensure_bparts(srw_ctx* h, size_t n) {
+  if (n <= h->bpart_cap) return SRW_OK;
+  size_t cap = std::max(n, 2 * h->bpart_cap);
+  destroy_graphs(h);
+  dfree(h->d_bpart);
+  SRW_CUDA(h, cudaMalloc(&h->d_bpart, sizeof(double) * cap), "batched partials");
+  h->bpart_cap = cap;
+  return SRW_OK;
+}
+
+static srw_status check_status_word(srw_ctx* h, cudaStream_t s, bool* domain) {
+  unsigned st = 0;
+  SRW_CUDA(h, cudaMemcpyAsync(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status read");
+  SRW_CUDA(h, cudaStreamSynchronize(s), "stream sync");
+  if (st) SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
+  if (st & kStatusTimeout) return fail(h, SRW_ETIMEOUT, "a bounded device wait expired; the fold aborted");
+  if (domain) *domain = (st & kStatusDomain) != 0;
+  return SRW_OK;
+}
+
+// Replays the cached graph for this call signature, capturing it first if needed.
+template <class Body>
+static srw_status run_graph(srw_ctx* h, int path, int precision, int P, const void* theta, void* out,
+                            cudaStream_t s, Body body) {
+  for (auto& g : h->graphs) {
+    if (g.path == path && g.precision == precision && g.P == P && g.theta == theta && g.out == out &&
+        g.stream == s && g.prof == h->profile) {
+      SRW_CUDA(h, cudaGraphLaunch(g.exec, s), "graph launch");
+      return SRW_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  SRW_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t eb = body(s);
+  cudaError_t ee = cudaStreamEndCapture(s, &graph);
+  if (eb != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, eb, "kernel launch during capture");
+  }
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(h, ei, "graph instantiate");
+  if (h->graphs.size() >= 32) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(GraphEntry{path, precision, P, h->profile, theta, out, s, exec});
+  SRW_CUDA(h, cudaGraphLaunch(exec, s), "graph launch");
+  return SRW_OK;
+}
+
+}  // namespace srw
+
+using namespace srw;
+
+extern "C" {
+
+const char* srw_status_string(srw_status s) {
+  switch (s) {
+    case SRW_OK: return "ok";
+    case SRW_EINVAL: return "invalid argument";
+    case SRW_ENOMEM: return "out of memory";
+    case SRW_ECUDA: return "CUDA error";
+    case SRW_ENODATA: return "no data set";
+    case SRW_EDOMAIN: return "expected count <= 0 where data > 0";
+    case SRW_ETIMEOUT: return "device wait timed out";
+    case SRW_EUNSUPPORTED: return "unsupported device";
+  }
+  return "unknown status";
+}
+
+const char* srw_last_error(srw_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_sources, const float* R,
+                      const srw_options* opt, srw_handle* out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, SRW_EINVAL, "out handle pointer is NULL");
+  *out = nullptr;
+  if (!bin || !sources || !R || !opt) return fail(nullptr, SRW_EINVAL, "NULL binning/sources/R/options");
+  if (bin->n_t < 1 || bin->n_rec < 1 || !bin->t_edges)
+    return fail(nullptr, SRW_EINVAL, "n_t and n_rec must be >= 1 and t_edges non-NULL");
+  if (bin->n_t > 49152) return fail(nullptr, SRW_EINVAL, "n_t above the supported maximum 49152");
+  if (n_sources < 1) return fail(nullptr, SRW_EINVAL, "need at least one source");
+  const int n_t = bin->n_t, n_rec = bin->n_rec;
+  if (!finite_all(bin->t_edges, (size_t)n_t + 1) || bin->t_edges[0] < 0.0)
+    return fail(nullptr, SRW_EINVAL, "t_edges must be finite and >= 0");
+  for (int i = 0; i < n_t; ++i)
+    if (!(bin->t_edges[i + 1] > bin->t_edges[i])) return fail(nullptr, SRW_EINVAL, "t_edges must ascend strictly");
+  double t_min = bin->t_min > 0.0 ? bin->t_min : 1e-3;
+  if (!std::isfinite(t_min)) return fail(nullptr, SRW_EINVAL, "t_min must be finite");
+  if (!(opt->exposure > 0.0) || !std::isfinite(opt->exposure))
+    return fail(nullptr, SRW_EINVAL, "exposure must be finite and > 0");
+  const double sin2w = opt->sin2w > 0.0 ? opt->sin2w : 0.23121;
+  const double f_tau = opt->f_tau >= 0.0 ? opt->f_tau : 0.5;
+  if (!(sin2w < 1.0) || !(f_tau <= 1.0)) return fail(nullptr, SRW_EINVAL, "sin2w must be < 1 and f_tau <= 1");
+  long long n_nodes = 0;
+  for (int k = 0; k < n_sources; ++k) {
+    const srw_source& s = sources[k];
+    if (s.n_nodes < 1 || !s.e || !s.w || !s.pee) return fail(nullptr, SRW_EINVAL, "source with no nodes or NULL arrays");
+    for (int n = 0; n < s.n_nodes; ++n) {
+      if (!(s.e[n] > 0.0) || !std::isfinite(s.e[n])) return fail(nullptr, SRW_EINVAL, "node energies must be > 0");
+      if (!(s.w[n] >= 0.0) || !std::isfinite(s.w[n])) return fail(nullptr, SRW_EINVAL, "node weights must be >= 0");
+      if (!(s.pee[n] >= 0.0 && s.pee[n] <= 1.0)) return fail(nullptr, SRW_EINVAL, "P_ee must lie in [0, 1]");
+    }
+    n_nodes += s.n_nodes;
+  }
+  if (n_nodes > (1 << 26)) return fail(nullptr, SRW_EINVAL, "too many nodes");
+  for (size_t q = 0; q < (size_t)n_rec * n_t; ++q)
+    if (!(R[q] >= 0.f) || !std::isfinite(R[q])) return fail(nullptr, SRW_EINVAL, "R must be finite and >= 0");
+  if (opt->e_true_sm) {
+    if (!finite_all(opt->e_true_sm, n_t)) return fail(nullptr, SRW_EINVAL, "e_true_sm must be finite");
+    for (int i = 0; i < n_t; ++i)
+      if (opt->e_true_sm[i] < 0.0) return fail(nullptr, SRW_EINVAL, "e_true_sm must be >= 0");
+  }
+
+  int dev = 0, ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(nullptr, SRW_ECUDA, "no CUDA device available");
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "cudaGetDevice failed");
+  cudaDeviceProp prop;
+  if ((ce = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "device properties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, SRW_EUNSUPPORTED, "this build targets sm_103a (GB300); device is sm_" +
+                                               std::to_string(prop.major) + std::to_string(prop.minor));
+
+  srw_ctx* h = new (std::nothrow) srw_ctx();
+  if (!h) return fail(nullptr, SRW_ENOMEM, "host allocation");
+  h->device = dev;
+  h->sm_count = prop.multiProcessorCount;
+  h->cc_major = prop.major;
+  h->cc_minor = prop.minor;
+  h->n_t = n_t;
+  h->n_rec = n_rec;
+  h->n_nodes = (int)n_nodes;
+  h->midpoint = bin->midpoint ? 1 : 0;
+  h->k_pad = (n_t + 63) / 64 * 64;
+  h->ld_r = h->k_pad;
+  h->rec_pad = (n_rec + 255) / 256 * 256;
+  h->t_min = t_min;
+  h->sin2w = sin2w;
+  h->f_tau = f_tau;
+  h->exposure = opt->exposure;
+  h->has_esm_input = opt->e_true_sm ? 1 : 0;
+  h->kappa = (kPi * kAlpha * kAlpha / (kMe * kMe)) / (2.0 * kGF * kGF * kMe / kPi) * kMuUnit * kMuUnit;
+
+  auto bail = [&](srw_status s) {
+    std::string msg = h->err;
+    release(h);
+    delete h;
+    fail(nullptr, s, msg);
+    return s;
+  };
+#define CREATE_CUDA(call, what)                       \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, what)); \
+  } while (0)
+
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking), "stream create");
+  cudaStream_t s = h->own_stream;
+
+  // ---- nodes: flavour weights in FP64, sorted by T_max descending
+  const int N = h->n_nodes;
+  std::vector<double> E(N), w(N), pe(N), pm(N), pt(N), tmax(N);
+  {
+    int q = 0;
+    for (int k = 0; k < n_sources; ++k)
+      for (int n = 0; n < sources[k].n_nodes; ++n, ++q) {
+        E[q] = sources[k].e[n];
+        w[q] = sources[k].w[n];
+        const double p = sources[k].pee[n];
+        pe[q] = p;
+        pm[q] = (1.0 - p) * (1.0 - f_tau);
+        pt[q] = (1.0 - p) * f_tau;
+        tmax[q] = 2.0 * E[q] * E[q] / (kMe + 2.0 * E[q]);
+      }
+  }
+  std::vector<int> order(N);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tmax[a] > tmax[b]; });
+  std::vector<float4> node_a(N), node_w(N), node_c(N), node_wlo(N);
+  std::vector<double> node64(5 * (size_t)N);
+  for (int q = 0; q < N; ++q) {
+    const int o = order[q];
+    const double e = E[o];
+    const double wq[4] = {w[o] * pe[o], w[o] * pm[o], w[o] * pt[o], w[o]};
+    node_w[q] = make_float4((float)wq[0], (float)wq[1], (float)wq[2], (float)wq[3]);
+    node_wlo[q] = make_float4((float)(wq[0] - (double)node_w[q].x), (float)(wq[1] - (double)node_w[q].y),
+                              (float)(wq[2] - (double)node_w[q].z), (float)(wq[3] - (double)node_w[q].w));
+    node64[q] = e;
+    node64[(size_t)N + q] = w[o] * pe[o];
+    node64[2 * (size_t)N + q] = w[o] * pm[o];
+    node64[3 * (size_t)N + q] = w[o] * pt[o];
+    node64[4 * (size_t)N + q] = w[o];
+  }
+
+  // ---- bins.  Every "does node n reach bin i" decision is made here in FP64
+  // and handed to the kernels as integers: k_n = number of bins that lie
+  // entirely below T_max(E_n) (integrated mode) or whose centre lies below it
+  // (midpoint mode).  Bins i < k_n are complete, bin k_n is clipped at T_max
+  // (integrated mode; its integrals are precomputed in FP64 per node), bins
+  // above get nothing.  Nodes are sorted by T_max descending, so k_n does not
+  // increase with n and the nodes reaching bin i are the prefix k_n >= i.
+  std::vector<float4> bin_f(n_t);
+  std::vector<float> bin_l(n_t);
+  std::vector<double> bin64(2 * (size_t)n_t);
+  std::vector<double> edge_hi(n_t), edge_c(n_t);
+  for (int i = 0; i < n_t; ++i) {
+    const double lo = bin->t_edges[i], hi = bin->t_edges[i + 1];
+    bin64[i] = lo;
+    bin64[(size_t)n_t + i] = hi;
+    edge_hi[i] = hi;
+    edge_c[i] = 0.5 * (lo + hi);
+    if (h->midpoint) {
+      const double tc = 0.5 * (lo + hi);
+      // bins whose centre is below the threshold carry zero width
+      bin_f[i] = make_float4((float)tc, tc >= t_min ? (float)(hi - lo) : 0.f, 0.f, 0.f);
+      bin_l[i] = 0.f;
+    } else {
+      const double a = std::max(lo, t_min);
+      if (!(hi > a)) {
+        bin_f[i] = make_float4(1.f, 1.f, 0.f, 0.f);  // below threshold: zero-width bin
+        bin_l[i] = 0.f;
+        continue;
+      }
+      bin_f[i] = make_float4((float)a, (float)hi, (float)(hi - a), (float)(0.5 * (hi - a) * (a + hi)));
+      bin_l[i] = (float)std::log1p((hi - a) / a);
+    }
+  }
+  std::vector<int> kn(N);
+  for (int q = 0; q < N; ++q) {
+    const double tm = tmax[order[q]], e = E[order[q]];
+    const std::vector<double>& ref = h->midpoint ? edge_c : edge_hi;
+    // number of bins with edge (hi or centre) below T_max: hi <= tm, centre < tm
+    int k;
+    if (h->midpoint)
+      k = (int)(std::lower_bound(ref.begin(), ref.end(), tm) - ref.begin());
+    else
+      k = (int)(std::upper_bound(ref.begin(), ref.end(), tm) - ref.begin());
+    kn[q] = k;
+    node_a[q] = make_float4((float)e, (float)(1.0 / e), int_bits_as_float(k), (float)(kMe / (e * e)));
+    node_c[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!h->midpoint && k < n_t) {
+      const double a = std::max(bin->t_edges[k], t_min), b = tm;
+      if (b > a) {
+        const double d = b - a, u = 1.0 - a / e, v = 1.0 - b / e;
+        node_c[q] = make_float4((float)d, (float)(0.5 * d * (a + b)), (float)(d * (u * u + u * v + v * v) / 3.0),
+                                (float)(std::log1p(d / a) - d / e));
+      }
+    }
+  }
+  // nodes with k_n >= i reach bin i (complete or clipped): a prefix because k_n is non-increasing
+  std::vector<int> bin_count(n_t + 1, 0);
+  for (int q = 0; q < N; ++q) bin_count[std::min(kn[q], n_t)] += 1;
+  for (int i = n_t - 1; i >= 0; --i) bin_count[i] += bin_count[i + 1];
+  bin_count.resize(n_t);
+  for (int i = 0; i < n_t; ++i)
+    if (!h->midpoint && !(bin->t_edges[i + 1] > std::max(bin->t_edges[i], t_min))) bin_count[i] = 0;
+
+  // ---- device tables
+  const size_t ld = h->ld_r;
+  CREATE_CUDA(dalloc(h, &h->d_node_a, N), "alloc nodes");
+  CREATE_CUDA(dalloc(h, &h->d_node_w, N), "alloc nodes");
+  CREATE_CUDA(dalloc(h, &h->d_node_c, N), "alloc nodes");
+  CREATE_CUDA(dalloc(h, &h->d_node_wlo, N), "alloc nodes");
+  CREATE_CUDA(dalloc(h, &h->d_node64, 5 * (size_t)N), "alloc nodes");
+  CREATE_CUDA(dalloc(h, &h->d_bin_count, n_t), "alloc bins");
+  CREATE_CUDA(dalloc(h, &h->d_bin_f, n_t), "alloc bins");
+  CREATE_CUDA(dalloc(h, &h->d_bin_l, n_t), "alloc bins");
+  CREATE_CUDA(dalloc(h, &h->d_bin64, 2 * (size_t)n_t), "alloc bins");
+  CREATE_CUDA(dalloc(h, &h->d_basis, (size_t)kNB * n_t), "alloc basis");
+  CREATE_CUDA(dalloc(h, &h->d_ssm64, n_t), "alloc");
+  CREATE_CUDA(dalloc(h, &h->d_esm64, n_t), "alloc");
+  CREATE_CUDA(dalloc(h, &h->d_ssm32, n_t), "alloc");
+  CREATE_CUDA(dalloc(h, &h->d_esm32, h->k_pad), "alloc");
+  CREATE_CUDA(dalloc(h, &h->d_shat, (size_t)kNB * h->k_pad), "alloc shat");
+  CREATE_CUDA(dalloc(h, &h->d_shat_lo, (size_t)kNB * h->k_pad), "alloc shat");
+  CREATE_CUDA(dalloc(h, &h->d_R, (size_t)n_rec * ld), "alloc R");
+  CREATE_CUDA(dalloc(h, &h->d_W, h->k_pad), "alloc W");
+  CREATE_CUDA(dalloc(h, &h->d_S, n_t), "alloc S");
+  CREATE_CUDA(dalloc(h, &h->d_musig, n_rec), "alloc");
+  CREATE_CUDA(dalloc(h, &h->d_muref64, n_rec), "alloc reference fold");
+  CREATE_CUDA(dalloc(h, &h->d_mu, n_rec), "alloc");
+  h->part_cap = fold_point_grid(h);
+  CREATE_CUDA(dalloc(h, &h->d_part, h->part_cap), "alloc partials");
+  CREATE_CUDA(dalloc(h, &h->d_ticket, 1), "alloc ticket");
+  CREATE_CUDA(dalloc(h, &h->d_status, 1), "alloc status");
+  CREATE_CUDA(dalloc(h, &h->d_theta0, 8), "alloc");
+  CREATE_CUDA(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned), s), "memset");
+  CREATE_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "memset");
+  CREATE_CUDA(cudaMemsetAsync(h->d_theta0, 0, sizeof(float) * 8, s), "memset");
+  CREATE_CUDA(cudaMemsetAsync(h->d_W, 0, sizeof(float) * h->k_pad, s), "memset");
+  CREATE_CUDA(cudaMemsetAsync(h->d_esm32, 0, sizeof(float) * h->k_pad, s), "memset");
+
+  CREATE_CUDA(cudaMemcpyAsync(h->d_node_a, node_a.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_node_w, node_w.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_node_c, node_c.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_node_wlo, node_wlo.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_node64, node64.data(), sizeof(double) * node64.size(), cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_count, bin_count.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_f, bin_f.data(), sizeof(float4) * n_t, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_l, bin_l.data(), sizeof(float) * n_t, cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemcpyAsync(h->d_bin64, bin64.data(), sizeof(double) * bin64.size(), cudaMemcpyHostToDevice, s), "upload");
+  CREATE_CUDA(cudaMemsetAsync(h->d_R, 0, sizeof(float) * (size_t)n_rec * ld, s), "memset R");
+  CREATE_CUDA(cudaMemcpy2DAsync(h->d_R, ld * sizeof(float), R, (size_t)n_t * sizeof(float), (size_t)n_t * sizeof(float),
+                                n_rec, cudaMemcpyHostToDevice, s), "upload R");
+  if (h->has_esm_input)
+    CREATE_CUDA(cudaMemcpyAsync(h->d_esm64, opt->e_true_sm, sizeof(double) * n_t, cudaMemcpyHostToDevice, s), "upload");
+
+  fold_point_init();
+  // ---- G0 coefficient spectra (FP64), S_SM, E_SM, shat; then S_SM of the FP32 kernel
+  CREATE_CUDA(launch_basis_fp64(h, s), "basis kernel");
+  CREATE_CUDA(launch_build_shat(h, s), "shat kernels");
+  CREATE_CUDA(launch_spectrum_point(h, h->d_theta0, nullptr, nullptr, h->d_ssm32, s), "SM spectrum kernel");
+  set_reference_coefs(h);  // reference point: the SM (theta = 0)
+  CREATE_CUDA(launch_reference_fold(h, s), "reference fold");
+  CREATE_CUDA(cudaStreamSynchronize(s), "create sync");
+  if (!h->has_esm_input && !(h->lambda > 0.0))
+    return bail(fail(h, SRW_EINVAL, "the SM spectrum folded through R is zero: cannot normalise the exposure"));
+
+  // ---- tensor-core path: BF16 hi/lo split of R and TMA descriptors
+  if (tc_supported(h)) {
+    CREATE_CUDA(dalloc(h, &h->d_rhi, (size_t)h->rec_pad * h->k_pad), "alloc R hi");
+    CREATE_CUDA(dalloc(h, &h->d_rlo, (size_t)h->rec_pad * h->k_pad), "alloc R lo");
+    CREATE_CUDA(dalloc(h, &h->d_shat_k8, (size_t)kNB * h->k_pad), "alloc shat k-major");
+    CREATE_CUDA(launch_split_r(h, s), "split R");
+    CREATE_CUDA(cudaStreamSynchronize(s), "split sync");
+    CREATE_CUDA(tc_prepare(h), "tensor map encode");
+    h->tensor_ok = true;
+  }
+  h->cfg[0] = FoldConfig{0, 128, 1, 0};
+  h->cfg[1] = h->cfg[2] = tc_num_configs() > 0 ? tc_config(0) : FoldConfig{0, 128, 1, 0};
+  *out = h;
+  return SRW_OK;
+#undef CREATE_CUDA
+}
+
+srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, int n_bkg,
+                        const unsigned char* mask) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!counts) return fail(h, SRW_EINVAL, "counts is NULL");
+  if (n_bkg < 0 || (n_bkg > 0 && !bkg)) return fail(h, SRW_EINVAL, "bad background arguments");
+  const int n_rec = h->n_rec;
+  for (int j = 0; j < n_rec; ++j)
+    if (!(counts[j] >= 0.0) || !std::isfinite(counts[j])) return fail(h, SRW_EINVAL, "counts must be finite and >= 0");
+  if (n_bkg > 0 && !finite_all(bkg, (size_t)n_bkg * n_rec)) return fail(h, SRW_EINVAL, "backgrounds must be finite");
+  cudaStream_t s = h->own_stream;
+  if (!h->d_n64) {
+    SRW_CUDA(h, dalloc(h, &h->d_n64, n_rec), "alloc data");
+    SRW_CUDA(h, dalloc(h, &h->d_b64, n_rec), "alloc data");
+    SRW_CUDA(h, dalloc(h, &h->d_nbm, n_rec), "alloc data");
+    SRW_CUDA(h, dalloc(h, &h->d_nb2, n_rec), "alloc data");
+    SRW_CUDA(h, dalloc(h, &h->d_cdata, 1), "alloc data");
+    SRW_CUDA(h, dalloc(h, &h->d_bref64, n_rec), "alloc data");
+  }
+  if (mask && !h->d_mask) SRW_CUDA(h, dalloc(h, &h->d_mask, n_rec), "alloc mask");
+  if (!mask) dfree(h->d_mask);
+  destroy_graphs(h);
+  double* d_bkg = nullptr;
+  SRW_CUDA(h, cudaMemcpyAsync(h->d_n64, counts, sizeof(double) * n_rec, cudaMemcpyHostToDevice, s), "upload counts");
+  if (mask) SRW_CUDA(h, cudaMemcpyAsync(h->d_mask, mask, n_rec, cudaMemcpyHostToDevice, s), "upload mask");
+  if (n_bkg > 0) {
+    SRW_CUDA(h, cudaMallocAsync(&d_bkg, sizeof(double) * (size_t)n_bkg * n_rec, s), "alloc bkg");
+    SRW_CUDA(h, cudaMemcpyAsync(d_bkg, bkg, sizeof(double) * (size_t)n_bkg * n_rec, cudaMemcpyHostToDevice, s), "upload bkg");
+  }
+  SRW_CUDA(h, launch_set_data(h, d_bkg, n_bkg, s), "data kernels");
+  if (d_bkg) SRW_CUDA(h, cudaFreeAsync(d_bkg, s), "free bkg");
+  SRW_CUDA(h, cudaStreamSynchronize(s), "set_data sync");
+  h->has_data = 1;
+  return SRW_OK;
+}
+
+srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out, int where, void* stream) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
+  if (stage < 0 || stage > 3) return fail(h, SRW_EINVAL, "stage must be 0..3");
+  if (stage == 3 && !h->has_data) return fail(h, SRW_ENODATA, "stage 3 needs srw_set_data");
+  cudaStream_t s = pick_stream(h, stream);
+  const float* th = theta;
+  if (where == SRW_HOST) {
+    for (int k = 0; k < 5; ++k)
+      if (!std::isfinite(theta[k])) return fail(h, SRW_EINVAL, "theta must be finite");
+    srw_status st = ensure_staging(h, 1);
+    if (st != SRW_OK) return st;
+    SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5, cudaMemcpyHostToDevice, s), "theta upload");
+    th = h->d_theta;
+  }
+  const bool dev = where == SRW_DEVICE;
+  const int n_out = stage <= 1 ? h->n_t : h->n_rec;
+  float* dst = dev ? out : (stage == 0 ? h->d_S : stage == 1 ? h->d_W : stage == 2 ? h->d_musig : h->d_mu);
+  if (stage == 0) {
+    SRW_CUDA(h, launch_spectrum_point(h, th, dst, nullptr, nullptr, s), "spectrum kernel");
+  } else {
+    // stage 1 returns the full W; stages 2 and 3 fold the deviation from the reference point
+    float* Wbuf = (stage == 1 && dev) ? out : h->d_W;
+    SRW_CUDA(h, launch_spectrum_point(h, th, nullptr, Wbuf, nullptr, s, stage >= 2), "spectrum kernel");
+    if (stage == 2) SRW_CUDA(h, launch_fold_point(h, h->d_W, dst, nullptr, nullptr, s, true), "fold kernel");
+    if (stage == 3) SRW_CUDA(h, launch_fold_point(h, h->d_W, nullptr, dst, nullptr, s, true), "fold kernel");
+  }
+  if (!dev) {
+    SRW_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(float) * n_out, cudaMemcpyDeviceToHost, s), "download");
+    SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  } else if (!stream) {
+    SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  }
+  return SRW_OK;
+}
+
+static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* out, int where, int precision,
+                              void* stream, bool points_only) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
+  if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
+  if (precision < SRW_FP32 || precision > SRW_BF16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (!h->has_data) return fail(h, SRW_ENODATA, "call srw_set_data first");
+  if (where != SRW_HOST && where != SRW_DEVICE) return fail(h, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
+  if (precision != SRW_FP32 && !h->tensor_ok)
+    return fail(h, SRW_EUNSUPPORTED, "tensor-core fold unavailable on this device");
+  cudaStream_t s = pick_stream(h, stream);
+  const float* th = theta;
+  double* o = out;
+  if (where == SRW_HOST) {
+    for (size_t q = 0; q < (size_t)P * 5; ++q)
+      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    srw_status st = ensure_staging(h, P);
+    if (st != SRW_OK) return st;
+    SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
+             "theta upload");
+    th = h->d_theta;
+    o = h->d_out;
+  }
+
+  srw_status st = SRW_OK;
+  if (points_only) {
+    st = run_graph(h, 3, precision, P, th, o, s, [&](cudaStream_t cs) {
+      for (int p = 0; p < P; ++p) {
+        cudaError_t e = launch_spectrum_point(h, th + 5 * (size_t)p, nullptr, h->d_W, nullptr, cs, true);
+        if (e != cudaSuccess) return e;
+        if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o + p, cs, true)) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+  } else if (P == 1 && precision == SRW_FP32) {
+    st = run_graph(h, 1, precision, P, th, o, s, [&](cudaStream_t cs) {
+      cudaError_t e = launch_spectrum_point(h, th, nullptr, h->d_W, nullptr, cs, true);
+      if (e != cudaSuccess) return e;
+      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o, cs, true)) != cudaSuccess) return e;
+      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      return cudaSuccess;
+    });
+  } else {
+    const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
+    st = ensure_bparts(h, (size_t)n_parts_max * P);
+    if (st != SRW_OK) return st;
+    const FoldConfig cfg = h->cfg[precision];
+    st = run_graph(h, 2, precision, P, th, o, s, [&](cudaStream_t cs) {
+      int n_parts = 0;
+      cudaError_t e;
+      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      e = precision == SRW_FP32 ? launch_fold_simt(h, th, P, h->d_bpart, cs, &n_parts)
+                                : launch_fold_tc(h, th, P, precision, cfg, h->d_bpart, cs, &n_parts);
+      if (e != cudaSuccess) return e;
+      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
+      return launch_reduce_parts(h, h->d_bpart, n_parts, P, o, cs);
+    });
+  }
+  if (st != SRW_OK) return st;
+  if (where == SRW_HOST) {
+    SRW_CUDA(h, cudaMemcpyAsync(out, o, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, s), "download");
+    bool domain = false;
+    st = check_status_word(h, s, &domain);
+    if (st != SRW_OK) return st;
+    if (domain) return fail(h, SRW_EDOMAIN, "expected count <= 0 in a bin with data: value is +inf");
+  } else if (!stream) {
+    SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  }
+  return SRW_OK;
+}
+
+srw_status srw_loglik(srw_handle h, const float* theta, int P, double* out, int where, srw_precision precision,
+                      void* stream) {
+  return loglik_impl(h, theta, P, out, where, (int)precision, stream, false);
+}
+
+srw_status srw_loglik_points(srw_handle h, const float* theta, int P, double* out, int where, void* stream) {
+  return loglik_impl(h, theta, P, out, where, SRW_FP32, stream, true);
+}
+
+srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* out, int where, srw_precision precision,
+                              void* stream) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
+  if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
+  if (precision < SRW_FP32 || precision > SRW_BF16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (precision != SRW_FP32 && !h->tensor_ok)
+    return fail(h, SRW_EUNSUPPORTED, "tensor-core fold unavailable on this device");
+  cudaStream_t s = pick_stream(h, stream);
+  const float* th = theta;
+  float* o = out;
+  float* d_tmp = nullptr;
+  if (where == SRW_HOST) {
+    for (size_t q = 0; q < (size_t)P * 5; ++q)
+      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    srw_status st = ensure_staging(h, P);
+    if (st != SRW_OK) return st;
+    SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
+             "theta upload");
+    th = h->d_theta;
+    SRW_CUDA(h, cudaMallocAsync(&d_tmp, sizeof(float) * (size_t)P * h->n_rec, s), "alloc spectra");
+    o = d_tmp;
+  }
+  int n_parts = 0;
+  cudaError_t e = precision == SRW_FP32
+                      ? launch_fold_simt(h, th, P, nullptr, s, &n_parts, o)
+                      : launch_fold_tc(h, th, P, (int)precision, h->cfg[precision], nullptr, s, &n_parts, o);
+  if (e == cudaSuccess) e = launch_add_ref(h, o, P, s);
+  if (e != cudaSuccess) {
+    if (d_tmp) cudaFreeAsync(d_tmp, s);
+    return cuda_fail(h, e, "batched fold");
+  }
+  if (where == SRW_HOST) {
+    SRW_CUDA(h, cudaMemcpyAsync(out, d_tmp, sizeof(float) * (size_t)P * h->n_rec, cudaMemcpyDeviceToHost, s),
+             "download");
+    SRW_CUDA(h, cudaFreeAsync(d_tmp, s), "free spectra");
+    bool dom = false;
+    srw_status st = check_status_word(h, s, &dom);
+    if (st != SRW_OK) return st;
+  } else if (!stream) {
+    SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  }
+  return SRW_OK;
+}
+
+srw_status srw_get_basis(srw_handle h, double* out) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!out) return fail(h, SRW_EINVAL, "out is NULL");
+  SRW_CUDA(h, cudaMemcpy(out, h->d_basis, sizeof(double) * kNB * (size_t)h->n_t, cudaMemcpyDeviceToHost), "download");
+  return SRW_OK;
+}
+
+srw_status srw_info(srw_handle h, srw_info_t* info) {
+  if (!h || !info) return fail(h, SRW_EINVAL, "NULL argument");
+  info->n_t = h->n_t;
+  info->n_rec = h->n_rec;
+  info->n_nodes = h->n_nodes;
+  info->k_pad = h->k_pad;
+  info->device = h->device;
+  info->sm_count = h->sm_count;
+  info->tensor_path = h->tensor_ok ? 1 : 0;
+  info->lambda = h->has_esm_input ? 0.0 : h->lambda;
+  info->device_bytes = h->device_bytes;
+  return SRW_OK;
+}
+
+srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char* cache_path, void* stream,
+                        int* chosen) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
+  if (!h->has_data) return fail(h, SRW_ENODATA, "call srw_set_data first");
+  if (chosen) *chosen = 0;
+  if (precision == SRW_FP32 || !h->tensor_ok) return SRW_OK;  // single SIMT configuration
+  const int pr = (int)precision;
+  std::string key;
+  {
+    std::ostringstream k;
+    k << "srw-fold prec=" << pr << " M=" << P << " N=" << h->n_rec << " K=" << h->k_pad << " sm=" << h->sm_count;
+    key = k.str();
+  }
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      if (line.compare(0, key.size(), key) == 0 && line.size() > key.size() + 1) {
+        const int idx = std::atoi(line.c_str() + key.size() + 1);
+        if (idx >= 0 && idx < tc_num_configs()) {
+          h->cfg[pr] = tc_config(idx);
+          h->cfg_index[pr] = idx;
+          destroy_graphs(h);
+          if (chosen) *chosen = idx;
+          return SRW_OK;
+        }
+      }
+    }
+  }
+  cudaStream_t s = pick_stream(h, stream);
+  srw_status st = ensure_staging(h, P);
+  if (st != SRW_OK) return st;
+  const int n_parts_max = h->rec_pad / 128;
+  st = ensure_bparts(h, (size_t)n_parts_max * P);
+  if (st != SRW_OK) return st;
+  // deterministic in-box points for timing
+  std::vector<float> th((size_t)P * 5);
+  for (size_t q = 0; q < th.size(); ++q) th[q] = (float)(0.3 * std::sin(0.7 * (double)q + 0.1)) + (q % 5 == 4 ? 1.5f : 0.f);
+  SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s), "upload");
+  cudaEvent_t e0, e1;
+  SRW_CUDA(h, cudaEventCreate(&e0), "event");
+  SRW_CUDA(h, cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  int best_i = 0;
+  for (int i = 0; i < tc_num_configs(); ++i) {
+    const FoldConfig c = tc_config(i);
+    int n_parts = 0;
+    cudaError_t e = launch_fold_tc(h, h->d_theta, P, pr, c, h->d_bpart, s, &n_parts);  // warm-up
+    if (e != cudaSuccess) continue;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) launch_fold_tc(h, h->d_theta, P, pr, c, h->d_bpart, s, &n_parts);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    bool dom = false;
+    if (check_status_word(h, s, &dom) != SRW_OK) continue;  // a timed-out configuration is never chosen
+    if (ms < best) {
+      best = ms;
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cfg[pr] = tc_config(best_i);
+  h->cfg_index[pr] = best_i;
+  destroy_graphs(h);
+  if (chosen) *chosen = best_i;
+  if (cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    o << key << " " << best_i << "\n";
+  }
+  return SRW_OK;
+}
+
+srw_status srw_set_reference(srw_handle h, const float* theta_ref) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (theta_ref) {
+    for (int k = 0; k < 5; ++k)
+      if (!std::isfinite(theta_ref[k])) return fail(h, SRW_EINVAL, "theta_ref must be finite");
+    for (int k = 0; k < 5; ++k) h->theta_ref[k] = theta_ref[k];
+    h->use_ref = 1;
+  } else {
+    h->use_ref = 0;
+  }
+  set_reference_coefs(h);
+  destroy_graphs(h);
+  cudaStream_t s = h->own_stream;
+  SRW_CUDA(h, launch_reference_fold(h, s), "reference fold");
+  if (h->has_data) SRW_CUDA(h, launch_data_ref(h, s), "data kernels");
+  SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  return SRW_OK;
+}
+
+srw_status srw_profile(srw_handle h, int enable) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (enable && !h->ev_fold[0]) {
+    SRW_CUDA(h, cudaEventCreate(&h->ev_fold[0]), "event create");
+    SRW_CUDA(h, cudaEventCreate(&h->ev_fold[1]), "event create");
+  }
+  h->profile = enable ? 1 : 0;
+  return SRW_OK;
+}
+
+srw_status srw_profile_read(srw_handle h, float* fold_ms) {
+  if (!h || !fold_ms) return fail(h, SRW_EINVAL, "NULL argument");
+  if (!h->profile) return fail(h, SRW_EINVAL, "profiling is not enabled");
+  SRW_CUDA(h, cudaEventSynchronize(h->ev_fold[1]), "event sync");
+  SRW_CUDA(h, cudaEventElapsedTime(fold_ms, h->ev_fold[0], h->ev_fold[1]), "event elapsed");
+  return SRW_OK;
+}
+
+srw_status srw_destroy(srw_handle h) {
+  if (!h) return SRW_OK;
+  cudaSetDevice(h->device);
+  if (h->own_stream) cudaStreamSynchronize(h->own_stream);
+  release(h);
+  delete h;
+  return SRW_OK;
+}
+
+}  // extern "C"

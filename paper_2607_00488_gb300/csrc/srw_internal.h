@@ -1,0 +1,202 @@
+// Internal state and launchers of the srw library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/srw.h"
+
+namespace srw {
+
+// Physical constants (CODATA 2018).
+constexpr double kMe = 0.51099895000;           // electron mass [MeV]
+constexpr double kAlpha = 1.0 / 137.035999084;  // fine-structure constant
+constexpr double kGF = 1.1663787e-11;           // Fermi constant [MeV^-2]
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMuUnit = 1.0e-11;             // mu_hat unit: 1e-11 Bohr magnetons
+
+// Number of coefficient spectra: the recoil spectrum is
+//   S(theta) = sum_b c_b(theta) B_b,
+//   c = {gLe^2, gRe^2, -gLe gRe, gLt^2, gRt^2, -gLt gRt, 1, mu_hat^2}.
+constexpr int kNB = 8;
+
+// Status bits written by kernels into the context's device status word.
+constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusDomain = 2u;
+
+// Device-side view of the theta-independent model tables.
+struct ModelView {
+  int n_t, n_rec, n_nodes, k_pad, ld_r, midpoint;
+  float t_min;
+  double t_min64;
+  // nodes sorted by T_max descending
+  const float4* node_a;  // {E, 1/E, k_n (int bits), m_e/E^2}; k_n = #bins with T_hi <= T_max(E)
+  const float4* node_w;  // {w P_e, w P_mu, w P_tau, w}
+  const float4* node_wlo;  // FP32 residuals of node_w (node_w + node_wlo = FP64 value)
+  const float4* node_c;  // FP64-exact integrals over the clipped bin k_n: {I0, I1, J, MM}
+  const double* node64;  // [5][n_nodes]: E, w P_e, w P_mu, w P_tau, w (FP64, same order)
+  const int* bin_count;  // per bin: nodes [0, count) may contribute
+  const float4* bin_f;   // {a = max(T_lo, t_min), b = T_hi, I0 = b - a, I1 = (b-a)(a+b)/2}
+  const float* bin_l;    // log(b/a) per bin (from FP64)
+  const double* bin64;   // [2][n_t]: T_lo, T_hi (FP64)
+  const float* ssm32;    // [n_t] S_SM from the FP32 spectrum kernel (weights denominator)
+  const float* esm32;    // [n_t] E_SM baseline
+  const float* R;        // [n_rec][ld_r] FP32, zero padded
+};
+
+// Data view for the likelihood epilogues.
+struct DataView {
+  int n_rec;
+  const double* n64;     // counts
+  const double* b64;     // summed background
+  const float4* nbm;     // {n_j, b_j, mask_j, 0} as floats for the batched epilogue
+  const unsigned char* mask;
+  const double* c_data;  // device scalar: 2 sum [n - n ln n + lnGamma(n+1)]
+};
+
+struct GraphEntry {
+  int path, precision, P, prof;
+  const void* theta;
+  void* out;
+  cudaStream_t stream;
+  cudaGraphExec_t exec;
+};
+
+// Coupling monomials of the reference point (double-float), subtracted from
+// those of each theta: the batched folds compute R (W(theta) - W_ref) and add
+// the FP64 reference fold R W_ref.
+struct CoefRef {
+  float hi[kNB], lo[kNB];
+};
+
+// Tile configuration of the batched fold.
+struct FoldConfig {
+  int kind;      // 0 = SIMT FP32, 1 = tcgen05
+  int bn;        // rec-bin tile (N)
+  int stages;
+  int w_warps;   // producer warps for the weighted-spectrum operand
+};
+
+}  // namespace srw
+
+struct srw_ctx {
+  int device = 0, sm_count = 0, cc_major = 0, cc_minor = 0;
+  int n_t = 0, n_rec = 0, n_nodes = 0, midpoint = 0;
+  int ld_r = 0;     // FP32 R row pitch (multiple of 4 floats)
+  int k_pad = 0;    // recoil dimension padded to 64 for the BF16 operands
+  int rec_pad = 0;  // n_rec padded to 256 rows for the BF16 split R
+  double t_min = 1e-3, sin2w = 0.23121, f_tau = 0.5, exposure = 0, lambda = 0, kappa = 0;
+  int has_esm_input = 0;
+  int has_data = 0;
+  size_t device_bytes = 0;
+
+  // model tables
+  float4* d_node_a = nullptr;
+  float4* d_node_w = nullptr;
+  float4* d_node_c = nullptr;
+  float4* d_node_wlo = nullptr;
+  double* d_node64 = nullptr;
+  int* d_bin_count = nullptr;
+  float4* d_bin_f = nullptr;
+  float* d_bin_l = nullptr;
+  double* d_bin64 = nullptr;
+  double* d_basis = nullptr;   // [8][n_t] FP64 coefficient spectra
+  double* d_ssm64 = nullptr;   // [n_t] FP64 S_SM
+  double* d_esm64 = nullptr;   // [n_t] FP64 E_SM
+  float* d_ssm32 = nullptr;
+  float* d_esm32 = nullptr;
+  float* d_shat = nullptr;     // [8][k_pad] FP32 pre-weighted basis (W = sum_b c_b shat_b)
+  float* d_shat_lo = nullptr;  // [8][k_pad] FP32 residuals of shat
+  float* d_shat_k8 = nullptr;  // [k_pad][8] FP32 shat, k-major (tensor-core W producers)
+  float* d_R = nullptr;        // [n_rec][ld_r]
+  __nv_bfloat16* d_rhi = nullptr;  // [rec_pad][k_pad]
+  __nv_bfloat16* d_rlo = nullptr;
+
+  // data
+  double* d_n64 = nullptr;
+  double* d_b64 = nullptr;
+  float4* d_nbm = nullptr;
+  float2* d_nb2 = nullptr;     // {n_j or -1 where masked, b_j + R W_ref} (tensor-core epilogue)
+  unsigned char* d_mask = nullptr;
+  double* d_cdata = nullptr;
+
+  // scratch (device)
+  float* d_W = nullptr;        // [ld_r] weighted true spectrum of the point path
+  float* d_S = nullptr;        // [n_t] spectrum of the point path
+  float* d_musig = nullptr;    // [n_rec]
+  float* d_mu = nullptr;       // [n_rec]
+  double* d_part = nullptr;    // partial sums (point path: per block)
+  int part_cap = 0;
+  unsigned* d_ticket = nullptr;
+  unsigned* d_status = nullptr;
+  double* d_bpart = nullptr;   // batched partials [n_tiles][P]
+  size_t bpart_cap = 0;
+  float* d_theta = nullptr;    // staging for host theta
+  double* d_out = nullptr;     // staging for host out
+  int stage_cap = 0;
+  float* d_theta0 = nullptr;   // 5 zeros
+
+  cudaStream_t own_stream = nullptr;
+  std::vector<srw::GraphEntry> graphs;
+  srw::FoldConfig cfg[3];      // per precision
+  int cfg_index[3] = {-1, -1, -1};
+  bool tensor_ok = false;
+  void* tmap = nullptr;        // TMA descriptors for R hi/lo (tcgen05 path)
+  int profile = 0;             // record events around the fold launch
+  int use_ref = 1;             // fold deviations from the reference point
+  float theta_ref[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  srw::CoefRef cref{};          // monomials of theta_ref (zeros when use_ref == 0)
+  float gref[2][10] = {};       // coupling products of theta_ref for the spectrum kernel (hi, lo)
+  double* d_muref64 = nullptr;  // [n_rec] R W_ref in FP64
+  double* d_bref64 = nullptr;   // [n_rec] R W_ref + background (FP64)
+  cudaEvent_t ev_fold[2] = {nullptr, nullptr};
+  std::string err;
+};
+
+namespace srw {
+
+srw_status fail(srw_ctx* h, srw_status s, const std::string& msg);
+srw_status cuda_fail(srw_ctx* h, cudaError_t e, const char* what);
+
+ModelView model_view(const srw_ctx* h);
+DataView data_view(const srw_ctx* h);
+
+// spectrum.cu
+cudaError_t launch_basis_fp64(const srw_ctx* h, cudaStream_t s);
+cudaError_t launch_spectrum_point(const srw_ctx* h, const float* theta, float* S_out, float* W_out,
+                                  float* ssm_out, cudaStream_t s, bool delta = false);
+cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s);
+cudaError_t launch_build_shat(srw_ctx* h, cudaStream_t s);
+
+// likelihood.cu
+cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStream_t s);
+cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s);
+cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s);
+int fold_point_grid(const srw_ctx* h);
+void fold_point_init();
+int fold_simt_parts(int n_rec);
+cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out, float* mu_out, double* out,
+                              cudaStream_t s, bool delta = false);
+cudaError_t launch_reduce_parts(const srw_ctx* h, const double* parts, int n_parts, int P, double* out,
+                                cudaStream_t s);
+
+// fold_simt.cu
+cudaError_t launch_fold_simt(const srw_ctx* h, const float* theta, int P, double* parts, cudaStream_t s,
+                             int* n_parts, float* musig_out = nullptr);
+
+// fold_tc.cu
+bool tc_supported(const srw_ctx* h);
+cudaError_t tc_prepare(srw_ctx* h);
+void tc_release(srw_ctx* h);
+int tc_num_configs();
+FoldConfig tc_config(int i);
+cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
+                           double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr);
+cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s);
+
+}  // namespace srw

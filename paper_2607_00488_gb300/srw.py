@@ -1,0 +1,321 @@
+"""ctypes binding of the srw C ABI (``include/srw.h``).
+
+Argument marshalling only: every computation runs in the CUDA library
+``libsrw.so``.  The functions carry the C names.  Host arguments are numpy
+arrays; device arguments are CUDA tensors (anything with ``data_ptr()`` and
+``is_cuda``), in which case the call is stream-ordered on the given stream
+(default: torch's current stream).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsrw.so")
+
+SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOUT, SRW_EUNSUPPORTED = range(8)
+SRW_HOST, SRW_DEVICE = 0, 1
+SRW_FP32, SRW_BF16, SRW_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3}
+
+# Entry points declared in include/srw.h (checked by the test-suite).
+EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "srw_loglik", "srw_loglik_points", "srw_get_basis",
+           "srw_autotune", "srw_info", "srw_set_reference", "srw_profile", "srw_profile_read", "srw_last_error", "srw_status_string",
+           "srw_destroy")
+
+
+class SrwError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("srw status %d: %s" % (status, message))
+        self.status = status
+
+
+class _Binning(ctypes.Structure):
+    _fields_ = [("n_t", ctypes.c_int), ("t_edges", ctypes.POINTER(ctypes.c_double)), ("n_rec", ctypes.c_int),
+                ("t_min", ctypes.c_double), ("midpoint", ctypes.c_int)]
+
+
+class _Source(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int), ("e", ctypes.POINTER(ctypes.c_double)),
+                ("w", ctypes.POINTER(ctypes.c_double)), ("pee", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("sin2w", ctypes.c_double), ("f_tau", ctypes.c_double), ("exposure", ctypes.c_double),
+                ("e_true_sm", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_t", ctypes.c_int), ("n_rec", ctypes.c_int), ("n_nodes", ctypes.c_int), ("k_pad", ctypes.c_int),
+                ("device", ctypes.c_int), ("sm_count", ctypes.c_int), ("tensor_path", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libsrw.so``; fails loudly if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsrw.so is not built (run paper_2607_00488_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+        L.srw_create.argtypes = [ctypes.POINTER(_Binning), ctypes.POINTER(_Source), ip, vp,
+                                 ctypes.POINTER(_Options), ctypes.POINTER(vp)]
+        L.srw_set_data.argtypes = [vp, dp, dp, ip, vp]
+        L.srw_spectrum.argtypes = [vp, fp, ip, fp, ip, vp]
+        L.srw_loglik.argtypes = [vp, fp, ip, vp, ip, ip, vp]
+        L.srw_spectrum_batch.argtypes = [vp, fp, ip, vp, ip, ip, vp]
+        L.srw_loglik_points.argtypes = [vp, fp, ip, vp, ip, vp]
+        L.srw_get_basis.argtypes = [vp, dp]
+        L.srw_autotune.argtypes = [vp, ip, ip, ctypes.c_char_p, vp, ctypes.POINTER(ctypes.c_int)]
+        L.srw_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        L.srw_set_reference.argtypes = [vp, vp]
+        L.srw_profile.argtypes = [vp, ip]
+        L.srw_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.srw_last_error.argtypes = [vp]
+        L.srw_last_error.restype = ctypes.c_char_p
+        L.srw_status_string.argtypes = [ip]
+        L.srw_status_string.restype = ctypes.c_char_p
+        L.srw_destroy.argtypes = [vp]
+        for name in EXPORTS:
+            if name not in ("srw_last_error", "srw_status_string"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, h):
+    if status != SRW_OK:
+        raise SrwError(status, lib().srw_last_error(h).decode(errors="replace"))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _is_device(x):
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------------ entry points
+def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False, sin2w=0.23121, f_tau=0.5,
+               e_true_sm=None):
+    """Create a context (see srw_create in include/srw.h).  Returns the handle."""
+    L = lib()
+    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    keep = [t_edges, R]
+    srcs = (_Source * len(sources))()
+    for k, s in enumerate(sources):
+        e = np.ascontiguousarray(s["e"], dtype=np.float64)
+        w = np.ascontiguousarray(s["w"], dtype=np.float64)
+        p = np.ascontiguousarray(s["pee"], dtype=np.float64)
+        keep += [e, w, p]
+        srcs[k] = _Source(e.size, _dptr(e), _dptr(w), _dptr(p))
+    b = _Binning(t_edges.size - 1, _dptr(t_edges), int(n_rec), float(t_min), 1 if midpoint else 0)
+    esm = None
+    if e_true_sm is not None:
+        esm = np.ascontiguousarray(e_true_sm, dtype=np.float64)
+        keep.append(esm)
+    o = _Options(float(sin2w), float(f_tau), float(exposure), _dptr(esm) if esm is not None else None)
+    h = ctypes.c_void_p()
+    st = L.srw_create(ctypes.byref(b), srcs, len(sources), R.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                      ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def srw_set_data(h, counts, bkg=None, mask=None):
+    counts = np.ascontiguousarray(counts, dtype=np.float64)
+    n_bkg = 0
+    bptr = None
+    if bkg is not None:
+        bkg = np.ascontiguousarray(np.atleast_2d(bkg), dtype=np.float64)
+        n_bkg = bkg.shape[0]
+        bptr = _dptr(bkg)
+    mptr = None
+    if mask is not None:
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        mptr = mask.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().srw_set_data(h, _dptr(counts), bptr, n_bkg, mptr), h)
+
+
+def srw_spectrum(h, theta, stage, out=None, stream=None):
+    """Spectrum stage 0..3 at one point.  Host theta -> numpy result; device
+    theta (CUDA tensor) -> result written into ``out`` (CUDA float32 tensor)."""
+    if _is_device(theta):
+        _check(lib().srw_spectrum(h, ctypes.c_void_p(theta.data_ptr()), int(stage), ctypes.c_void_p(out.data_ptr()),
+                                  SRW_DEVICE, _stream(stream)), h)
+        return out
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(5)
+    info = srw_info(h)
+    n = info["n_t"] if stage <= 1 else info["n_rec"]
+    res = np.empty(n, dtype=np.float32) if out is None else out
+    _check(lib().srw_spectrum(h, th.ctypes.data_as(ctypes.c_void_p), int(stage), res.ctypes.data_as(ctypes.c_void_p),
+                              SRW_HOST, None), h)
+    return res
+
+
+def _loglik(fn, h, theta, precision, out, stream, extra_prec=True):
+    if _is_device(theta):
+        P = theta.numel() // 5
+        args = [h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()), SRW_DEVICE]
+        if extra_prec:
+            args.append(int(precision))
+        args.append(_stream(stream))
+        _check(fn(*args), h)
+        return out
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
+    P = th.shape[0]
+    res = np.empty(P, dtype=np.float64) if out is None else out
+    args = [h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p), SRW_HOST]
+    if extra_prec:
+        args.append(int(precision))
+    args.append(None)
+    st = fn(*args)
+    if st == SRW_EDOMAIN:
+        return res  # +inf marks the points outside the domain
+    _check(st, h)
+    return res
+
+
+def srw_loglik(h, theta, precision=SRW_FP32, out=None, stream=None):
+    """-2 ln L for P points (theta: P x 5 float32)."""
+    return _loglik(lib().srw_loglik, h, theta, precision, out, stream)
+
+
+def srw_loglik_points(h, theta, out=None, stream=None):
+    """The plain single-point path applied to each point in turn."""
+    return _loglik(lib().srw_loglik_points, h, theta, None, out, stream, extra_prec=False)
+
+
+def srw_spectrum_batch(h, theta, precision=SRW_FP32, out=None, stream=None):
+    """Folded signal spectra [P, n_rec] (float32) from the batched fold."""
+    if _is_device(theta):
+        P = theta.numel() // 5
+        _check(lib().srw_spectrum_batch(h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()),
+                                        SRW_DEVICE, int(precision), _stream(stream)), h)
+        return out
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
+    P = th.shape[0]
+    n_rec = srw_info(h)["n_rec"]
+    res = np.empty((P, n_rec), dtype=np.float32) if out is None else out
+    _check(lib().srw_spectrum_batch(h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p),
+                                    SRW_HOST, int(precision), None), h)
+    return res
+
+
+def srw_get_basis(h):
+    info = srw_info(h)
+    out = np.empty((8, info["n_t"]), dtype=np.float64)
+    _check(lib().srw_get_basis(h, _dptr(out)), h)
+    return out
+
+
+def srw_autotune(h, P, precision, cache_path=None, stream=None):
+    chosen = ctypes.c_int(-1)
+    cp = cache_path.encode() if cache_path else None
+    _check(lib().srw_autotune(h, int(P), int(precision), cp, _stream(stream) if stream is not None else None,
+                              ctypes.byref(chosen)), h)
+    return chosen.value
+
+
+def srw_info(h):
+    i = _Info()
+    _check(lib().srw_info(h, ctypes.byref(i)), h)
+    return {"n_t": i.n_t, "n_rec": i.n_rec, "n_nodes": i.n_nodes, "k_pad": i.k_pad, "device": i.device,
+            "sm_count": i.sm_count, "tensor_path": bool(i.tensor_path), "lambda": i.lambda_,
+            "device_bytes": i.device_bytes}
+
+
+def srw_set_reference(h, theta_ref):
+    """Reference point of the folds (5 values), or None to fold directly."""
+    if theta_ref is None:
+        _check(lib().srw_set_reference(h, None), h)
+        return
+    t = np.ascontiguousarray(theta_ref, dtype=np.float32).reshape(5)
+    _check(lib().srw_set_reference(h, t.ctypes.data_as(ctypes.c_void_p)), h)
+
+
+def srw_profile(h, enable):
+    _check(lib().srw_profile(h, 1 if enable else 0), h)
+
+
+def srw_profile_read(h):
+    """Device milliseconds of the fold launch of the last srw_loglik call."""
+    ms = ctypes.c_float()
+    _check(lib().srw_profile_read(h, ctypes.byref(ms)), h)
+    return ms.value
+
+
+def srw_last_error(h):
+    return lib().srw_last_error(h).decode(errors="replace")
+
+
+def srw_destroy(h):
+    if h:
+        lib().srw_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience
+class Likelihood:
+    """Owns one srw context built from a workload dict (see ``workloads``)."""
+
+    def __init__(self, wl, counts=None, midpoint=False, e_true_sm=None, mask=None):
+        self.handle = srw_create(wl["t_edges"], wl["R"].shape[0], wl["sources"], wl["R"], wl["exposure"],
+                                 t_min=wl["t_min"], midpoint=midpoint, sin2w=wl["sin2w"], f_tau=wl["f_tau"],
+                                 e_true_sm=e_true_sm)
+        if counts is not None:
+            srw_set_data(self.handle, counts, wl.get("bkg"), mask)
+
+    def spectrum(self, theta, stage, out=None, stream=None):
+        return srw_spectrum(self.handle, theta, stage, out, stream)
+
+    def loglik(self, theta, precision=SRW_FP32, out=None, stream=None):
+        return srw_loglik(self.handle, theta, precision, out, stream)
+
+    def spectrum_batch(self, theta, precision=SRW_FP32, out=None, stream=None):
+        return srw_spectrum_batch(self.handle, theta, precision, out, stream)
+
+    def loglik_points(self, theta, out=None, stream=None):
+        return srw_loglik_points(self.handle, theta, out, stream)
+
+    def set_reference(self, theta_ref):
+        srw_set_reference(self.handle, theta_ref)
+
+    def basis(self):
+        return srw_get_basis(self.handle)
+
+    def info(self):
+        return srw_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            srw_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,75 @@
+"""The C-ABI library: builds, loads, exports every declared entry point, and
+rejects invalid arguments on the host before touching a device."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def srw():
+    from paper_2607_00488_gb300 import build
+    build.build()
+    import paper_2607_00488_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "srw.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(srw_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("srw_create", "srw_set_data", "srw_spectrum", "srw_loglik", "srw_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(srw):
+    lib = srw.lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(srw.EXPORTS) >= set(_declared())
+
+
+def test_status_strings(srw):
+    lib = srw.lib()
+    assert lib.srw_status_string(0) == b"ok"
+    assert lib.srw_status_string(5).startswith(b"expected count")
+
+
+def _args(**kw):
+    wl = {
+        "t_edges": np.linspace(0.0, 1.0, 9),
+        "n_rec": 4,
+        "sources": [{"e": np.array([0.862]), "w": np.array([1.0]), "pee": np.array([0.55])}],
+        "R": np.full((4, 8), 0.2, dtype=np.float32),
+        "exposure": 100.0,
+    }
+    wl.update(kw)
+    return wl
+
+
+@pytest.mark.parametrize("bad", [
+    {"t_edges": np.array([0.0, 0.5, 0.4, 1.0])},                      # not ascending
+    {"t_edges": np.array([0.0, np.nan, 1.0])},                         # NaN edge
+    {"R": np.full((4, 8), -0.1, dtype=np.float32)},                    # negative response
+    {"exposure": 0.0},
+    {"sources": [{"e": np.array([-1.0]), "w": np.array([1.0]), "pee": np.array([0.5])}]},
+    {"sources": [{"e": np.array([1.0]), "w": np.array([1.0]), "pee": np.array([1.5])}]},
+    {"n_rec": 0},
+])
+def test_create_rejects_invalid_arguments(srw, bad):
+    a = _args(**bad)
+    r = a["R"]
+    if a["n_rec"] == 0:
+        r = np.zeros((1, 8), dtype=np.float32)
+    with pytest.raises(srw.SrwError) as ei:
+        srw.srw_create(a["t_edges"], a["n_rec"], a["sources"], r, a["exposure"])
+    assert ei.value.status == 1  # SRW_EINVAL, raised before any device call

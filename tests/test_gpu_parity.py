@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances
+* FP64 create-time coefficient spectra: 1e-10 relative.
+* FP32 spectra (single-point kernels): per-bin relative error <= 1e-6.
+* -2 ln L in the fit region (points near the reference point, where a fit
+  or a confidence interval is decided): |d| <= 1e-4 for the FP32 paths and
+  |d| <= 1e-3 for the BF16 hi+lo (3-product) path.
+* -2 ln L everywhere: a fold whose per-bin results carry relative errors
+  delta_j changes -2 ln L by about 2 sum_j (1 - n_j/mu_j) mu_j delta_j, so far
+  from the data (mu - n large) the same per-bin precision gives a larger d.
+  Every point must satisfy |d| <= tol + 2 * B with the measured budget
+  B = 2 sum_j |1 - n_j/mu_j| |dmu_j| (dmu_j: the same path's per-bin error),
+  i.e. the likelihood reduction adds no error of its own.
+* BF16 single product: per-bin relative error <= 2 * 2^-8 (both operands are
+  rounded to 8 significant bits).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP32_BIN = 1e-6
+TOL_FP32_LL = 1e-4
+TOL_BF16X3_LL = 1e-3
+TOL_BF16_BIN = 2.0 * 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def srw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2607_00488_gb300 as pkg
+    return pkg
+
+
+class Case:
+    def __init__(self, srw, wl, with_data=True, mask=None, **kw):
+        self.wl = wl
+        self.counts = workloads.load_counts(wl["name"]) if with_data else None
+        self.lk = srw.Likelihood(wl, self.counts, mask=mask, **kw)
+        self.ref = O.OracleModel.from_workload(wl, **kw)
+        if with_data:
+            self.ref.set_data(self.counts, wl["bkg"], mask)
+
+
+@pytest.fixture(scope="module")
+def be7(srw):
+    c = Case(srw, workloads.be7_line_workload())
+    yield c
+    c.lk.close()
+
+
+@pytest.fixture(scope="module")
+def solar(srw):
+    c = Case(srw, workloads.solar_set_workload())
+    yield c
+    c.lk.close()
+
+
+def near_sm(n, seed):
+    """Points in the fit region around the SM reference: |eps| <= 0.02, mu_hat <= 0.5."""
+    rng = np.random.default_rng(seed)
+    th = np.zeros((n, 5), np.float32)
+    th[:, :4] = rng.uniform(-0.02, 0.02, (n, 4))
+    th[:, 4] = rng.uniform(0.0, 0.5, n)
+    return th
+
+
+def _rel_bins(got, want, floor):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    big = np.abs(want) > floor
+    rel = np.abs(got[big] - want[big]) / np.abs(want[big])
+    absd = np.abs(got[~big] - want[~big])
+    return (rel.max() if rel.size else 0.0), (absd.max() if absd.size else 0.0)
+
+
+def _budget(case, th, mu_sig_gpu):
+    """B = 2 sum_j |1 - n_j/mu_j| |dmu_j| from the measured per-bin errors."""
+    mu = case.ref.mu(th.astype(np.float64))
+    dmu = np.asarray(mu_sig_gpu, np.float64) - case.ref.mu_sig(th.astype(np.float64))
+    n = case.counts
+    on = mu > 0
+    return 2.0 * np.sum(np.abs(1.0 - n[on] / mu[on]) * np.abs(dmu[on]))
+
+
+# ---------------------------------------------------------------- create-time basis
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_coefficient_spectra_fp64(name, request):
+    c = request.getfixturevalue(name)
+    wl = c.wl
+    want = O.coefficient_spectra(wl["sources"], wl["t_edges"], wl["t_min"], wl["sin2w"], wl["f_tau"])
+    got = c.lk.basis()
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-13 * np.abs(want).max())
+
+
+# ---------------------------------------------------------------- single-point spectra
+def _thetas(n=3, seed=21):
+    rng = np.random.default_rng(seed)
+    th = [np.zeros(5, np.float32), np.array([0.1, -0.2, 0.05, 0.3, 2.0], np.float32)]
+    for _ in range(n):
+        th.append(np.concatenate([rng.uniform(-0.3, 0.3, 4), rng.uniform(0, 3, 1)]).astype(np.float32))
+    return th
+
+
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_spectrum_stage0_fp32(name, request):
+    c = request.getfixturevalue(name)
+    for th in _thetas():
+        want = c.ref.spectrum(th.astype(np.float64))
+        got = c.lk.spectrum(th, 0)
+        rel, absd = _rel_bins(got, want, 1e-4 * np.abs(want).max())
+        assert rel <= TOL_FP32_BIN, (th, rel)
+        assert absd <= 1e-4 * TOL_FP32_BIN * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_weighted_spectrum_stage1(name, request):
+    c = request.getfixturevalue(name)
+    for th in _thetas():
+        want = c.ref.weighted_true(th.astype(np.float64))
+        rel, _ = _rel_bins(c.lk.spectrum(th, 1), want, 1e-4 * np.abs(want).max())
+        assert rel <= TOL_FP32_BIN, (th, rel)
+
+
+def test_weights_identically_one_at_sm(be7):
+    # W(theta = 0) is E_SM itself: S(0)/S_SM is exactly 1 on the device
+    w0 = be7.lk.spectrum(np.zeros(5, np.float32), 1)
+    rel, _ = _rel_bins(w0, be7.ref.e_sm, 1e-6 * be7.ref.e_sm.max())
+    assert rel <= 1e-6
+    np.testing.assert_array_equal(w0, be7.lk.spectrum(np.zeros(5, np.float32), 1))
+
+
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_fold_stages(name, request):
+    c = request.getfixturevalue(name)
+    for th in _thetas(n=1):
+        want = c.ref.mu_sig(th.astype(np.float64))
+        rel, _ = _rel_bins(c.lk.spectrum(th, 2), want, 1e-3 * want.max())
+        assert rel <= TOL_FP32_BIN, rel
+        want_mu = c.ref.mu(th.astype(np.float64))
+        rel, _ = _rel_bins(c.lk.spectrum(th, 3), want_mu, 1e-3 * want_mu.max())
+        assert rel <= TOL_FP32_BIN, rel
+
+
+# ---------------------------------------------------------------- likelihood, fit region
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_loglik_fit_region_all_paths(srw, name, request):
+    c = request.getfixturevalue(name)
+    th = np.concatenate([np.zeros((1, 5), np.float32), near_sm(9, 3)])
+    want = c.ref.neg2lnl_batch(th.astype(np.float64))
+    single = np.array([c.lk.loglik(t[None, :], srw.SRW_FP32)[0] for t in th])
+    points = c.lk.loglik_points(th)
+    fp32 = c.lk.loglik(th, srw.SRW_FP32)
+    x3 = c.lk.loglik(th, srw.SRW_BF16X3)
+    assert np.max(np.abs(single - want)) <= TOL_FP32_LL, single - want
+    assert np.max(np.abs(points - want)) <= TOL_FP32_LL, points - want
+    assert np.max(np.abs(fp32 - want)) <= TOL_FP32_LL, fp32 - want
+    assert np.max(np.abs(x3 - want)) <= TOL_BF16X3_LL, x3 - want
+
+
+# ---------------------------------------------------------------- likelihood, everywhere
+@pytest.mark.parametrize("name,prec,tol", [
+    ("be7", "fp32", TOL_FP32_LL), ("be7", "bf16x3", TOL_BF16X3_LL),
+    ("solar", "fp32", TOL_FP32_LL), ("solar", "bf16x3", TOL_BF16X3_LL),
+])
+def test_loglik_within_measured_budget(srw, name, prec, tol, request):
+    c = request.getfixturevalue(name)
+    th = np.concatenate([c.wl["theta"][:8], workloads.theta_box(5, 11)])
+    p = srw.PRECISIONS[prec]
+    got = c.lk.loglik(th, p)
+    spectra = c.lk.spectrum_batch(th, p)
+    for k in range(th.shape[0]):
+        want = c.ref.neg2lnl(th[k].astype(np.float64))
+        b = _budget(c, th[k], spectra[k])
+        assert abs(got[k] - want) <= tol + 2.0 * b, (k, got[k] - want, b)
+
+
+def test_single_point_within_measured_budget(srw, solar):
+    th = workloads.theta_box(4, 12)
+    for t in th:
+        got = solar.lk.loglik(t[None, :], srw.SRW_FP32)[0]
+        want = solar.ref.neg2lnl(t.astype(np.float64))
+        b = _budget(solar, t, solar.lk.spectrum(t, 2))
+        assert abs(got - want) <= TOL_FP32_LL + 2.0 * b, (got - want, b)
+
+
+# ---------------------------------------------------------------- batched spectra per bin
+@pytest.mark.parametrize("prec,tol", [("fp32", TOL_FP32_BIN), ("bf16x3", 2e-5), ("bf16", TOL_BF16_BIN)])
+def test_batched_spectra_per_bin(srw, solar, prec, tol):
+    th = np.concatenate([np.zeros((1, 5), np.float32), workloads.theta_box(130, 13)])  # two point tiles, ragged
+    got = solar.lk.spectrum_batch(th, srw.PRECISIONS[prec])
+    for k in (0, 1, 64, 127, 128, 130):
+        want = solar.ref.mu_sig(th[k].astype(np.float64))
+        rel, _ = _rel_bins(got[k], want, 1e-3 * want.max())
+        assert rel <= tol, (k, rel)
+
+
+def test_bf16_raw_fold_without_reference(srw, solar):
+    # the reference point switched off: every product is rounded to BF16
+    th = workloads.theta_box(3, 14)
+    try:
+        solar.lk.set_reference(None)
+        got = solar.lk.spectrum_batch(th, srw.SRW_BF16)
+    finally:
+        solar.lk.set_reference(np.zeros(5))
+    for k in range(3):
+        want = solar.ref.mu_sig(th[k].astype(np.float64))
+        rel, _ = _rel_bins(got[k], want, 1e-3 * want.max())
+        assert rel <= TOL_BF16_BIN, rel
+
+
+def test_reference_point_moves(srw, be7):
+    th = near_sm(4, 5) + np.array([0.1, 0.0, 0.0, 0.0, 0.0], np.float32)
+    want = be7.ref.neg2lnl_batch(th.astype(np.float64))
+    try:
+        be7.lk.set_reference(np.array([0.1, 0.0, 0.0, 0.0, 0.0]))
+        x3 = be7.lk.loglik(th, srw.SRW_BF16X3)
+        fp32 = be7.lk.loglik(th, srw.SRW_FP32)
+    finally:
+        be7.lk.set_reference(np.zeros(5))
+    assert np.max(np.abs(x3 - want)) <= TOL_BF16X3_LL
+    assert np.max(np.abs(fp32 - want)) <= TOL_FP32_LL
+
+
+def test_batched_agrees_with_single_point_path(srw, solar):
+    th = np.concatenate([np.zeros((1, 5), np.float32), near_sm(63, 6)])
+    single = solar.lk.loglik_points(th)
+    batched = solar.lk.loglik(th, srw.SRW_FP32)
+    assert np.max(np.abs(single - batched)) <= TOL_FP32_LL
+
+
+def test_full_scan_sampled(srw, solar):
+    # the benchmark's launch: 65,536 points in one call, sampled against the oracle
+    th = workloads.theta_box(65536, 3)
+    th[:4] = near_sm(4, 8)
+    dev = torch.device("cuda")
+    out = torch.empty(65536, dtype=torch.float64, device=dev)
+    solar.lk.loglik(torch.tensor(th, device=dev), srw.SRW_BF16X3, out=out)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    idx = [0, 1, 2, 3, 127, 65535]
+    for k in idx:
+        want = solar.ref.neg2lnl(th[k].astype(np.float64))
+        if k < 4:
+            assert abs(got[k] - want) <= TOL_BF16X3_LL
+        else:
+            b = _budget(solar, th[k], solar.lk.spectrum_batch(th[k:k + 1], srw.SRW_BF16X3)[0])
+            assert abs(got[k] - want) <= TOL_BF16X3_LL + 2.0 * b
