@@ -205,6 +205,30 @@ srw_status srw_set_reference(srw_handle h, const float* theta_ref);
 srw_status srw_profile(srw_handle h, int enable);
 srw_status srw_profile_read(srw_handle h, float* fold_ms);
 
+/* Allocation-free single-point likelihood (the paper has no counterpart; it
+ * serves callers that cannot allocate device memory: code running inside
+ * another framework's memory manager, which owns every device allocation, or
+ * code that must not call cudaMalloc/cudaFree because they can synchronise the
+ * device).  No handle and no allocation: every argument is a device pointer on
+ * the current device, owned by the caller; the call is stream-ordered on
+ * `stream` and returns before the result is ready.
+ *   R:      n_rec x ld float32 response, row-major, zero beyond the last true bin
+ *   W:      ld float32 weighted true spectrum (e.g. from srw_spectrum stage 1)
+ *   counts: n_rec observed counts; bkg: n_rec summed background or NULL;
+ *   mask:   n_rec live-bin mask or NULL;  out: 1 double, -2 ln L (eq. logL)
+ * of mu_j = M_j (sum_i R_ji W_i + bkg_j), folded in FP32 like the single-
+ * point path with the reference point disabled.
+ * Limits: 1 <= n_rec <= 65536, ld a positive multiple of 64, R and W 16-byte
+ * aligned; larger sizes are rejected with SRW_EINVAL (message from
+ * srw_noalloc_last_error).  The kernels' scratch is a fixed static device array
+ * of about 8 KB shared by every call: calls that overlap on the GPU race on it,
+ * so serialise them (one stream).  The first call on each device resolves that
+ * array's device address and sets a kernel attribute; make that first call
+ * before any stream capture. */
+srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld, const float* W, const double* counts,
+                                    const double* bkg, const unsigned char* mask, double* out, void* stream);
+const char* srw_noalloc_last_error(void);
+
 const char* srw_last_error(srw_handle h);
 const char* srw_status_string(srw_status s);
 srw_status srw_destroy(srw_handle h);

@@ -25,6 +25,7 @@ from .srw import (  # noqa: F401
     srw_info,
     srw_last_error,
     srw_loglik,
+    srw_loglik_point_noalloc,
     srw_loglik_points,
     srw_profile,
     srw_set_reference,

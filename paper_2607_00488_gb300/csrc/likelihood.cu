@@ -12,6 +12,9 @@
 // Poisson term and the bin reduction are FP64 and fused into the same launch
 // (the last block to finish sums the per-block partials in block order).
 
+#include <mutex>
+#include <string>
+
 #include "dfloat.cuh"
 #include "poisson.cuh"
 #include "ptx.cuh"
@@ -308,3 +311,105 @@ cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s) 
 }
 
 }  // namespace srw
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-point likelihood.
+//
+// For callers that cannot allocate device memory themselves: code that runs
+// inside another framework's memory manager, which owns every device
+// allocation, or code that must not call cudaMalloc/cudaFree because those
+// calls can synchronise the whole device.  They pass all inputs and the output
+// as device pointers; the scratch the kernels need (per-block partial sums,
+// the data-only constant of -2 ln L, the last-block ticket and the status
+// word) lives in the file-scope array below, which every GPU that loads this
+// library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace srw {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;  // partial sums: one per block of the fold
+constexpr int kNoAllocMaxRec = 65536;    // reconstructed bins
+struct NoAllocScratch {
+  double parts[kNoAllocMaxBlocks];
+  double c_data;
+  unsigned ticket;
+  unsigned status;
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+struct NoAllocDevice {
+  NoAllocScratch* scratch = nullptr;  // device address of g_noalloc_scratch
+  int sm_count = 0;
+  bool ready = false;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+}  // namespace
+}  // namespace srw
+
+static std::mutex g_noalloc_mutex;
+static thread_local std::string g_noalloc_err;
+
+extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld, const float* W,
+                                               const double* counts, const double* bkg, const unsigned char* mask,
+                                               double* out, void* stream) {
+  using namespace srw;
+  auto bad = [](const char* m) {
+    g_noalloc_err = m;
+    return SRW_EINVAL;
+  };
+  if (!R || !W || !counts || !out) return bad("R, W, counts and out must be device pointers");
+  if (n_rec < 1 || n_rec > kNoAllocMaxRec) return bad("n_rec must lie in [1, 65536]");
+  if (ld < 64 || ld % 64 != 0) return bad("ld must be a positive multiple of 64");
+  if (((uintptr_t)R % 16) != 0 || ((uintptr_t)W % 16) != 0) return bad("R and W must be 16-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_noalloc_err = cudaGetErrorString(e);
+    return SRW_ECUDA;
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return bad("device index out of range");
+  NoAllocDevice& nd = g_noalloc_dev[dev];
+  {
+    // once per device, with that device current: resolve the device address
+    // of the scratch array (its host-side name is only a stand-in)
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!nd.ready) {
+      void* p = nullptr;
+      if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&nd.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(fold_point_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+              cudaSuccess) {
+        g_noalloc_err = cudaGetErrorString(e);
+        return SRW_ECUDA;
+      }
+      nd.scratch = static_cast<NoAllocScratch*>(p);
+      nd.ready = true;
+    }
+  }
+  const int g = nd.sm_count > 0 ? nd.sm_count : 148;
+  const int rpb = (n_rec + g - 1) / g;
+  const int grid = (n_rec + rpb - 1) / rpb;
+  if (grid > kNoAllocMaxBlocks) return bad("too many blocks for the scratch array");
+  const int chunk = ld < kGvChunk ? ld : kGvChunk;
+  const size_t smem = sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * (size_t)kGvConsumers * rpb;
+  if (smem > 200 * 1024) return bad("n_rec too large for the fold's shared memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  NoAllocScratch* sc = nd.scratch;
+  // the array keeps the previous call's contents: the ticket and the status must start at zero
+  if ((e = cudaMemsetAsync(&sc->ticket, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) {
+    g_noalloc_err = cudaGetErrorString(e);
+    return SRW_ECUDA;
+  }
+  cdata_kernel<<<1, 1024, 0, s>>>(counts, mask, n_rec, &sc->c_data);
+  fold_point_kernel<<<grid, kGvThreads, smem, s>>>(R, n_rec, ld, rpb, W, nullptr, counts, bkg, mask, &sc->c_data,
+                                                    nullptr, nullptr, sc->parts, &sc->ticket, out, &sc->status);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    g_noalloc_err = cudaGetErrorString(e);
+    return SRW_ECUDA;
+  }
+  return SRW_OK;
+}
+
+extern "C" const char* srw_noalloc_last_error(void) { return g_noalloc_err.c_str(); }

@@ -25,7 +25,7 @@ PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3}
 # Entry points declared in include/srw.h (checked by the test-suite).
 EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "srw_loglik", "srw_loglik_points", "srw_get_basis",
            "srw_autotune", "srw_info", "srw_set_reference", "srw_profile", "srw_profile_read", "srw_last_error", "srw_status_string",
-           "srw_destroy")
+           "srw_destroy", "srw_loglik_point_noalloc", "srw_noalloc_last_error")
 
 
 class SrwError(RuntimeError):
@@ -84,8 +84,11 @@ def lib():
         L.srw_status_string.argtypes = [ip]
         L.srw_status_string.restype = ctypes.c_char_p
         L.srw_destroy.argtypes = [vp]
+        L.srw_loglik_point_noalloc.argtypes = [vp, ip, ip, vp, vp, vp, vp, vp, vp]
+        L.srw_noalloc_last_error.argtypes = []
+        L.srw_noalloc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("srw_last_error", "srw_status_string"):
+            if name not in ("srw_last_error", "srw_status_string", "srw_noalloc_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -260,6 +263,19 @@ def srw_profile_read(h):
     ms = ctypes.c_float()
     _check(lib().srw_profile_read(h, ctypes.byref(ms)), h)
     return ms.value
+
+
+def srw_loglik_point_noalloc(R, W, counts, out, bkg=None, mask=None, stream=None):
+    """Allocation-free single-point -2 ln L: every argument a CUDA tensor.
+    R: (n_rec, ld) float32 with ld a multiple of 64; W: (ld,) float32;
+    counts, bkg: (n_rec,) float64; mask: (n_rec,) uint8 or None; out: (1,) float64."""
+    n_rec, ld = R.shape
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = lib().srw_loglik_point_noalloc(ptr(R), int(n_rec), int(ld), ptr(W), ptr(counts), ptr(bkg), ptr(mask),
+                                        ptr(out), _stream(stream))
+    if st != SRW_OK:
+        raise SrwError(st, lib().srw_noalloc_last_error().decode(errors="replace"))
+    return out
 
 
 def srw_last_error(h):
