@@ -140,8 +140,9 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
 
 /* -2 ln L (without pull terms) for P parameter points.
  *   theta: P x 5 float32; out: P float64.
- * P == 1 with SRW_FP32 runs the single-point path (spectrum kernel, HBM-
- * streaming fold, fused Poisson reduction); otherwise the batched path (one
+ * P == 1 with SRW_FP32 runs the single-point path (weighted spectrum from
+ * the coefficient spectra, HBM-streaming fold, fused Poisson reduction);
+ * otherwise the batched path (one
  * persistent fold launch over all points with the Poisson reduction fused
  * into its epilogue) in the requested precision.  Each distinct
  * (path, precision, P, theta, out, stream) call signature is captured once
@@ -150,9 +151,11 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
 srw_status srw_loglik(srw_handle h, const float* theta, int P, double* out, int where,
                       srw_precision precision, void* stream);
 
-/* The plain single-point FP32 path applied to P points one after another:
- * per point one spectrum launch and one fold launch, in order (replayed from
- * a captured CUDA graph per call signature, like srw_loglik). */
+/* The plain single-point FP32 path applied to P points one after another, as
+ * the paper's pipeline does it (Sec. IV.B): per point the cross-section
+ * integrals are recomputed over all (node, bin) pairs by the spectrum kernel,
+ * then one HBM-streaming fold; launches in order, replayed from a captured
+ * CUDA graph per call signature, like srw_loglik. */
 srw_status srw_loglik_points(srw_handle h, const float* theta, int P, double* out, int where, void* stream);
 
 /* Folded signal spectra for P points with the batched fold:

@@ -46,27 +46,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Device-wide nanosecond clock.
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for phase `parity` of `bar` to complete.  Gives up after `limit_ns`
-// or when *abort becomes non-zero (another role gave up); returns false then.
+// Wait for phase `parity` of `bar` to complete.  Gives up after about
+// `limit_ns` (measured on the SM cycle counter, assuming ~2 GHz) or when
+// *abort becomes non-zero (another role gave up); returns false then.  The
+// clock and the abort flag are consulted only every 1024 polls (every 16
+// with a back-off), so a wait that succeeds soon costs no clock reads.
 // sleep_ns > 0 backs off between polls (for waits that are expected to be
 // long, so that the waiting warp does not take issue slots from others).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile unsigned* abort,
                                           uint64_t limit_ns = 2000000000ull, unsigned sleep_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
+  const uint32_t check_mask = sleep_ns ? 15u : 1023u;
+  const long long limit_cycles = (long long)(limit_ns * 2ull);
+  long long t0 = -1;
   for (uint32_t it = 1;; ++it) {
     if (sleep_ns) __nanosleep(sleep_ns);
     if (mbar_try_wait(bar, parity)) return true;
-    if (sleep_ns || (it & 63u) == 0) {
+    if ((it & check_mask) == 0) {
       if (abort != nullptr && *abort != 0u) return false;
-      if (globaltimer() - t0 > limit_ns) return false;
+      const long long now = clock64();
+      if (t0 < 0) t0 = now;
+      else if (now - t0 > limit_cycles) return false;
     }
   }
 }

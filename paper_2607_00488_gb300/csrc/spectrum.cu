@@ -143,23 +143,25 @@ spectrum_point_kernel(ModelView m, const float* __restrict__ theta, dfloat sin2w
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const int first = (blockIdx.x / kSpecCluster) * kBinsPerBlock;
-  if (threadIdx.x == 0) {
-    // couplings (eq. g_tilde) in double-float arithmetic; nu_mu is unshifted
+  if (threadIdx.x < 10) {
+    // couplings (eq. g_tilde) in double-float arithmetic, one product per
+    // thread; nu_mu is unshifted
+    const int k = threadIdx.x;
     const dfloat gle = df_add(df_add(dfloat{0.5f, 0.f}, sin2w), theta[0]);
     const dfloat gre = df_add(sin2w, theta[1]);
     const dfloat glt = df_add(df_add(dfloat{-0.5f, 0.f}, sin2w), theta[2]);
     const dfloat grt = df_add(sin2w, theta[3]);
     const dfloat glm = df_add(dfloat{-0.5f, 0.f}, sin2w), grm = sin2w;
-    const dfloat c[10] = {df_mul(gle, gle), df_mul(glm, glm), df_mul(glt, glt), df_mul(gre, gre),
-                          df_mul(grm, grm), df_mul(grt, grt), df_mul(gle, gre), df_mul(glm, grm),
-                          df_mul(glt, grt), df_mul(kappa, two_prod(theta[4], theta[4]))};
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-      // delta mode: monomials of theta minus those of the reference point
-      const dfloat d = delta ? df_add(c[k], dfloat{-gref.v[0][k], -gref.v[1][k]}) : c[k];
-      coef[0][k] = d.hi;
-      coef[1][k] = d.lo;
-    }
+    // order: gLe^2 gLm^2 gLt^2 gRe^2 gRm^2 gRt^2 gLe.gRe gLm.gRm gLt.gRt kappa mu^2
+    const dfloat x = k == 0 ? gle : k == 1 ? glm : k == 2 ? glt : k == 3 ? gre : k == 4 ? grm : k == 5 ? grt
+                   : k == 6 ? gle : k == 7 ? glm : k == 8 ? glt : kappa;
+    const dfloat y = k == 0 ? gle : k == 1 ? glm : k == 2 ? glt : k == 3 ? gre : k == 4 ? grm : k == 5 ? grt
+                   : k == 6 ? gre : k == 7 ? grm : k == 8 ? grt : two_prod(theta[4], theta[4]);
+    const dfloat c = df_mul(x, y);
+    // delta mode: monomials of theta minus those of the reference point
+    const dfloat d = delta ? df_add(c, dfloat{-gref.v[0][k], -gref.v[1][k]}) : c;
+    coef[0][k] = d.hi;
+    coef[1][k] = d.lo;
   }
   if (threadIdx.x < kBinsPerBlock) {
     const int i = first + threadIdx.x;
@@ -341,6 +343,45 @@ __global__ void shat_kernel(const double* __restrict__ basis, const double* __re
   }
 }
 
+// Weighted true spectrum of one point from the coefficient spectra (the
+// recoil spectrum is a polynomial in the coupling monomials, Sec. II):
+//   dW_i = sum_b (c_b(theta) - c_b(theta_ref)) shat_b,i
+// with monomials and shat as hi + lo float pairs (delta = 0: the full W).
+__global__ void weights_from_basis_kernel(const float* __restrict__ theta, dfloat sin2w, CoefRef cref,
+                                          const float* __restrict__ shat, const float* __restrict__ shat_lo,
+                                          int k_pad, float* __restrict__ W) {
+  __shared__ float ch[kNB], cl[kNB];
+  if (threadIdx.x < kNB) {
+    const dfloat s = sin2w;
+    const dfloat gle = df_add(df_add(dfloat{0.5f, 0.f}, s), theta[0]), gre = df_add(s, theta[1]);
+    const dfloat glt = df_add(df_add(dfloat{-0.5f, 0.f}, s), theta[2]), grt = df_add(s, theta[3]);
+    const int b = threadIdx.x;
+    dfloat c;
+    if (b == 0) c = df_mul(gle, gle);
+    else if (b == 1) c = df_mul(gre, gre);
+    else if (b == 2) { c = df_mul(gle, gre); c = dfloat{-c.hi, -c.lo}; }
+    else if (b == 3) c = df_mul(glt, glt);
+    else if (b == 4) c = df_mul(grt, grt);
+    else if (b == 5) { c = df_mul(glt, grt); c = dfloat{-c.hi, -c.lo}; }
+    else if (b == 6) c = dfloat{1.f, 0.f};
+    else c = two_prod(theta[4], theta[4]);
+    const dfloat d = df_add(c, dfloat{-cref.hi[b], -cref.lo[b]});
+    ch[b] = d.hi;
+    cl[b] = d.lo;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k_pad) return;
+  float a = 0.f, t = 0.f;
+#pragma unroll
+  for (int b = 0; b < kNB; ++b) {
+    const float sh = shat[(size_t)b * k_pad + i], sl = shat_lo[(size_t)b * k_pad + i];
+    a = fmaf(ch[b], sh, a);
+    t = fmaf(cl[b], sh, fmaf(ch[b], sl, t));
+  }
+  W[i] = a + t;
+}
+
 // Reference fold (create / set-reference time, FP64):
 //   W_ref,i = sum_b c_b(theta_ref) B_b,i E_SM,i / S_SM,i   (E_SM,i where S_SM,i = 0)
 //   mu_ref,j = sum_i R_ji W_ref,i
@@ -386,6 +427,12 @@ cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s) {
   muref_kernel<<<h->n_rec, 256, 0, s>>>(h->d_R, h->ld_r, h->n_t, d_w, h->d_muref64);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaFreeAsync(d_w, s);
+}
+
+cudaError_t launch_weights_from_basis(const srw_ctx* h, const float* theta, float* W, cudaStream_t s) {
+  weights_from_basis_kernel<<<(h->k_pad + 255) / 256, 256, 0, s>>>(theta, df_from_double(h->sin2w), h->cref,
+                                                                  h->d_shat, h->d_shat_lo, h->k_pad, W);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_basis_fp64(const srw_ctx* h, cudaStream_t s) {

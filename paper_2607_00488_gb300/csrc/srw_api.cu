@@ -608,7 +608,8 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
     });
   } else if (P == 1 && precision == SRW_FP32) {
     st = run_graph(h, 1, precision, P, th, o, s, [&](cudaStream_t cs) {
-      cudaError_t e = launch_spectrum_point(h, th, nullptr, h->d_W, nullptr, cs, true);
+      // W(theta) - W_ref from the coefficient spectra, then the HBM-streaming fold
+      cudaError_t e = launch_weights_from_basis(h, th, h->d_W, cs);
       if (e != cudaSuccess) return e;
       if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
       if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o, cs, true)) != cudaSuccess) return e;

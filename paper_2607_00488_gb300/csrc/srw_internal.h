@@ -171,6 +171,7 @@ cudaError_t launch_basis_fp64(const srw_ctx* h, cudaStream_t s);
 cudaError_t launch_spectrum_point(const srw_ctx* h, const float* theta, float* S_out, float* W_out,
                                   float* ssm_out, cudaStream_t s, bool delta = false);
 cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s);
+cudaError_t launch_weights_from_basis(const srw_ctx* h, const float* theta, float* W, cudaStream_t s);
 cudaError_t launch_build_shat(srw_ctx* h, cudaStream_t s);
 
 // likelihood.cu

@@ -6,9 +6,11 @@ code that must not call cudaMalloc/cudaFree because those calls can
 synchronise the device).  srw_loglik_point_noalloc serves them: the caller
 passes every input and the output as device memory, and the kernels' scratch
 is a fixed static device array inside the library.  This test calls it through
-the C ABI and checks it against the existing single-point entry point
-(srw_loglik with one point, reference point disabled so that both fold W
-directly), twice in a row, since consecutive calls share the scratch array.
+the C ABI and checks it against the existing single-point entry point that
+performs the same arithmetic (srw_loglik_points: the weighted spectrum from
+the cross-section integrals, then the fold, with the reference point disabled
+so that both fold W directly), twice in a row, since consecutive calls share
+the scratch array.
 """
 
 import numpy as np
@@ -44,7 +46,7 @@ def test_no_alloc_entry_point_matches_loglik():
         for th in thetas:
             W = torch.zeros(ld, dtype=torch.float32, device=dev)
             lk.spectrum(torch.from_numpy(th).to(dev), 1, out=W)
-            want = lk.loglik(th[None, :], srw.SRW_FP32)[0]
+            want = lk.loglik_points(th[None, :])[0]
             for _ in range(2):
                 out = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
                 srw.srw_loglik_point_noalloc(R, W, c, out, bkg=b)
