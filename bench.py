@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--points", type=int, default=65536)
     ap.add_argument("--cpu-sample", type=int, default=12, help="theta points for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true", help="skip the 64-configuration grouped measurement")
+    ap.add_argument("--grouped-only", action="store_true",
+                    help="only the grouped measurement (for profiling its launch)")
     return ap.parse_args()
 
 
@@ -209,6 +212,64 @@ def recorded_traffic(kernel_file, tag):
     return None
 
 
+# --------------------------------------------------------------------------- grouped workload
+def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src):
+    """64 uneven detector configurations (N_T 512-8192, N_rec 256-4096, 256-4096
+    points each, exposures 1e4-1e7) in one persistent fold launch per step."""
+    import numpy as np
+    import torch
+
+    gw = workloads.uneven_groups_workload()
+    counts = workloads.load_group_counts(gw)
+    members, thetas, useful = [], [], 0.0
+    for g, spec in enumerate(gw["groups"]):
+        wl = workloads.uneven_group_inputs(gw, g)
+        members.append(srw.Likelihood(wl, counts[g]))
+        thetas.append(wl["theta"])
+        useful += 2.0 * spec["n_rec"] * spec["n_t"] * spec["p"]
+    P = [spec["p"] for spec in gw["groups"]]
+    grp = srw.GroupedLikelihood(members, P)
+    cand = grp.autotune(prec)
+    sched = grp.schedule(prec)
+    th = torch.tensor(np.concatenate(thetas), device=dev)
+    out = torch.empty(th.shape[0], dtype=torch.float64, device=dev)
+    grp.profile(True)
+    for _ in range(args.warmup):
+        flush.add_(1.0)
+        grp.loglik(th, prec, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms, fold_ms = [], []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        grp.loglik(th, prec, out=out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        fold_ms.append(grp.profile_read())
+    grp.profile(False)
+    fold_s = statistics.mean(fold_ms) * 1e-3
+    peak = peaks["bf16_tflops"] / (3.0 if prec == srw.SRW_BF16X3 else 1.0)
+    n_pts = int(th.shape[0])
+    res = {
+        "workload": gw["name"], "configurations": len(P), "points": n_pts,
+        "evals_s": n_pts * args.steps / (sum(step_ms) * 1e-3), "ms_per_step": statistics.mean(step_ms),
+        "launches_per_step": 2,
+        "roofline": {"bound": "tensor", "achieved": useful / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": useful / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel (grouped)",
+                     "useful_tflop_per_launch": useful / 1e12, "fold_ms": statistics.mean(fold_ms),
+                     "peak_source": "%s (bf16 burst%s)" % (peak_src, " / 3 products" if prec == srw.SRW_BF16X3 else "")},
+        "schedule": {"candidate": cand, "bn_max": sched["bn_max"], "items": sched["n_items"], "ctas": sched["n_cta"],
+                     "configs_bn128": sum(1 for b in sched["bn"] if b == 128)},
+    }
+    grp.close()
+    for m in members:
+        m.close()
+    return res
+
+
 # --------------------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -229,6 +290,14 @@ def main():
         dist.init_process_group("gloo", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+
+    if args.grouped_only:
+        stream = torch.cuda.current_stream(dev)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        prec = srw.PRECISIONS["bf16x3" if args.precision == "auto" else args.precision]
+        peaks, peak_src = measured_peaks()
+        print(json.dumps(grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)))
+        return 0
 
     P = args.points
     wl = workloads.batched_scan_workload(P, theta_seed=3 + rank)
@@ -357,6 +426,8 @@ def main():
     }
     if clk:
         line["clocks"] = clk
+    if world == 1 and not args.no_grouped and prec != srw.SRW_FP32:
+        line["grouped"] = grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         idx, vals, dt, fit = oracle_subprocess(P, args.cpu_sample, 3, n_fit)
         d = [abs(gpu_vals[i] - v) for i, v in zip(idx, vals)]

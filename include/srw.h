@@ -232,6 +232,60 @@ srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld, const flo
                                     const double* bkg, const unsigned char* mask, double* out, void* stream);
 const char* srw_noalloc_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Grouped evaluation: several detector configurations (each an srw_handle with
+ * its own binning, response, data and reference point) evaluated in ONE
+ * persistent fold launch, so that configurations of very different sizes
+ * share the GPU without one launch per configuration.  Each configuration's
+ * -2 ln L is the same quantity srw_loglik gives for that handle (eq. logL);
+ * the paper evaluates one configuration at a time, the grouping is a batching
+ * of the same computation.
+ */
+typedef struct srw_group_ctx* srw_group;
+
+/* Group n handles (n >= 1, all on one device, each with data set) with P[g]
+ * points for handle g (P[g] >= 0, sum >= 1).  The handles are not owned and
+ * must outlive the group; later srw_set_data / srw_set_reference calls on a
+ * member are picked up by the next group call.  The group builds one work
+ * schedule per precision on first use (see srw_group_autotune). */
+srw_status srw_group_create(const srw_handle* handles, int n, const int* P, srw_group* out);
+
+/* -2 ln L of every point of every configuration.
+ *   theta: (sum_g P[g]) x 5 float32, configuration 0's points first, then
+ *          configuration 1's, ...;  out: sum_g P[g] float64 in the same order.
+ * SRW_BF16 / SRW_BF16X3: one persistent tensor-core launch over all
+ * configurations (work items = 128-point x bn-bin tiles, bn = 128 or 256 per
+ * configuration, assigned to CTAs longest-first onto the least-loaded CTA),
+ * then one reduction launch.  SRW_FP32: the SIMT fold of each configuration
+ * in turn, then the same reduction.  `where` and `stream` as in srw_loglik;
+ * host calls return SRW_EDOMAIN when a value is +inf. */
+srw_status srw_group_loglik(srw_group g, const float* theta, double* out, int where, srw_precision precision,
+                            void* stream);
+
+/* Time the candidate schedules for `precision` and keep the fastest:
+ *   0: every configuration with bn = 256;
+ *   1: bn per configuration from a cost model of its padded tiles;
+ *   2: every configuration with bn = 128 (shallower stages, more of them).
+ * `chosen` (may be NULL) receives the candidate index.  No-op for SRW_FP32. */
+srw_status srw_group_autotune(srw_group g, srw_precision precision, void* stream, int* chosen);
+
+/* Use candidate schedule `candidate` (0, 1 or 2 as above) for `precision`
+ * without timing (a fixed choice, or one read back from srw_group_schedule). */
+srw_status srw_group_set_schedule(srw_group g, srw_precision precision, int candidate);
+
+/* The schedule in use for `precision` (built if needed): widest tile, the tile
+ * width of each configuration (bn: n ints, may be NULL), work items, CTAs and
+ * the candidate index. */
+srw_status srw_group_schedule(srw_group g, srw_precision precision, int* bn_max, int* bn, int* n_items,
+                              int* n_cta, int* candidate);
+
+/* Device time of the last grouped fold launch (as srw_profile / srw_profile_read). */
+srw_status srw_group_profile(srw_group g, int enable);
+srw_status srw_group_profile_read(srw_group g, float* fold_ms);
+
+const char* srw_group_last_error(srw_group g);
+srw_status srw_group_destroy(srw_group g);
+
 const char* srw_last_error(srw_handle h);
 const char* srw_status_string(srw_status s);
 srw_status srw_destroy(srw_handle h);

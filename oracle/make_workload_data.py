@@ -31,6 +31,16 @@ def sm_counts(wl):
 
 
 def main():
+    gw = workloads.uneven_groups_workload()
+    parts = []
+    for g in range(len(gw["groups"])):
+        wl = workloads.uneven_group_inputs(gw, g)
+        parts.append(sm_counts(wl))
+    path = workloads.group_counts_path(gw["name"])
+    np.savetxt(path, np.concatenate(parts), fmt="%d",
+               header="%s: Poisson(SM expectation) per configuration, seed 0 each, "
+                      "configurations concatenated in order" % gw["name"])
+    print(path, len(parts))
     for name, make in workloads.WORKLOADS.items():
         wl = make()
         n = sm_counts(wl)

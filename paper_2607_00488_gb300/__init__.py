@@ -15,6 +15,7 @@ from .srw import (  # noqa: F401
     SRW_EDOMAIN,
     SRW_FP32,
     SRW_HOST,
+    GroupedLikelihood,
     Likelihood,
     SrwError,
     lib,
@@ -22,6 +23,14 @@ from .srw import (  # noqa: F401
     srw_create,
     srw_destroy,
     srw_get_basis,
+    srw_group_autotune,
+    srw_group_create,
+    srw_group_destroy,
+    srw_group_loglik,
+    srw_group_profile,
+    srw_group_profile_read,
+    srw_group_schedule,
+    srw_group_set_schedule,
     srw_info,
     srw_last_error,
     srw_loglik,

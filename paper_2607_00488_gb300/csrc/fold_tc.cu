@@ -30,6 +30,12 @@
 // all accumulating in FP32 in TMEM.  The accumulator is double-buffered
 // (2 x BN columns) so the epilogue of one tile overlaps the next tile's MMAs.
 //
+// Grouped launches (several detector configurations with their own binning,
+// response, data and points in one persistent grid) use the same kernel: each
+// work item names its configuration, whose descriptor (tensor maps, spectra,
+// per-bin constants, tile width) the roles read per item.  The host builds the
+// item lists (see group.cu).
+//
 // Every wait is bounded (ptx.cuh); on a timeout the CTA raises
 // kStatusTimeout, drains its outstanding copies and MMAs, frees TMEM and ends.
 
@@ -86,22 +92,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    ptx::smem_addr(bar))
                : "memory");
-}
-
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane.
@@ -184,13 +174,63 @@ struct TcShape {
   static constexpr int kTmemCols = 2 * BN;
 };
 
-template <int BN, bool X3>
+constexpr int kMaxGroups = 4096;  // configurations of one grouped launch
+
+// Kernel parameters.  A single-configuration launch walks the m x n tiles of
+// g0 with a grid stride; a grouped launch walks per-CTA item lists.
+struct TcLaunch {
+  TcGroup g0;                  // single configuration (its maps are kernel parameters of their own)
+  const TcGroup* groups;       // grouped: one per configuration (nullptr: single)
+  const int4* items;           // grouped: slot k * gridDim.x + b = {group, m0, n0, 0}, CTA b's k-th item
+  int n_items;                 // single: m_tiles x n_tiles; grouped: slots
+  const float* theta;          // [points][5]; a group's points start at p_off
+  double* parts;
+  float* musig_out;            // single configuration only: [P][n_rec] folded deviations
+  unsigned* status;
+};
+
+// Item loops: a grid stride written directly in blockIdx / gridDim / a kernel
+// parameter, which the compiler can see are warp-uniform.  Loop bounds taken
+// from memory (per-CTA list offsets) made the fold 6-8% slower: the loops hold
+// .sync.aligned tcgen05 instructions and bounded waits.  A grouped launch
+// therefore stores CTA b's k-th item at slot k * gridDim.x + b, and each list
+// ends with a stop item (group < 0).
+#define FOR_ITEMS(idx) for (int idx = (int)blockIdx.x; idx < L.n_items; idx += (int)gridDim.x)
+
+// Configuration (by value) and tile origin of work item idx (gi < 0: a stop
+// item of a grouped launch).  A single-
+// configuration launch takes its descriptor from the kernel parameters, so its
+// fields stay constant-bank operands (no address of a parameter is taken).
+template <bool GROUPED, int BN>
+__device__ __forceinline__ TcGroup work_at(const TcLaunch& L, int idx, int& m0, int& n0, int& gi) {
+  if (!GROUPED) {
+    const int nt = L.g0.n_tiles;
+    m0 = (idx / nt) * kBM;
+    n0 = (idx % nt) * BN;
+    gi = 0;
+    return L.g0;
+  }
+  const int4 it = L.items[idx];
+  m0 = it.y;
+  n0 = it.z;
+  gi = it.x;
+  return L.groups[it.x < 0 ? 0 : it.x];
+}
+
+// Orders the host's writes of a tensor map in global memory before its use
+// by the TMA unit (tensormap proxy).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
+// BN: widest rec tile of the launch; it fixes the shared-memory stages and the
+// TMEM accumulators.  In a grouped launch each configuration's tile width
+// bn <= BN is a runtime value (TMA box, MMA N, epilogue columns); a single
+// configuration uses bn = BN.
+template <int BN, bool X3, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
-fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-               const float* __restrict__ theta, int P, dfloat sin2w, CoefRef cref,
-               const float4* __restrict__ shat_k8, int k_pad,
-               int n_rec, const float2* __restrict__ nb2, double* __restrict__ parts,
-               float* __restrict__ musig_out, unsigned* __restrict__ status) {
+fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcLaunch L) {
   using S = TcShape<BN, X3>;
   constexpr int ST = S::kStages;
   extern __shared__ unsigned char dsmem_raw[];
@@ -199,12 +239,12 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   __shared__ __align__(8) uint64_t s_full[kShatSlots], s_empty[kShatSlots];
   __shared__ uint32_t tmem_slot;
   __shared__ unsigned abort_flag;
+  __shared__ uint32_t map_fenced[GROUPED ? kMaxGroups / 32 : 1];  // maps already acquired by the R producer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tiles = (P + kBM - 1) / kBM;
-  const int n_tiles = (n_rec + BN - 1) / BN;
-  const int n_work = m_tiles * n_tiles;
-  const int n_kb = k_pad / kBK;
+  unsigned* status = L.status;
+  double* const parts = L.parts;
+  float* const musig_out = L.musig_out;
 
   auto a_hi = [&](int st) { return smem + (size_t)st * S::kStageBytes; };
   auto a_lo = [&](int st) { return smem + (size_t)st * S::kStageBytes + S::kAB; };
@@ -214,6 +254,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     return reinterpret_cast<float4*>(smem + (size_t)ST * S::kStageBytes + (size_t)slot * kShatBytes);
   };
 
+  if (GROUPED)
+    for (int i = threadIdx.x; i < kMaxGroups / 32; i += blockDim.x) map_fenced[i] = 0u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       ptx::mbar_init(&r_full[s], 1);
@@ -251,14 +293,19 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     const int rg = lane;
     const int ch = warp;  // 16-byte chunk = 8 consecutive k
     int g = 0;            // global K-block counter (stage ring position)
-    for (int work = blockIdx.x; work < n_work; work += gridDim.x) {
+    FOR_ITEMS(idx) {
       if (__any_sync(0xffffffffu, aborted(&abort_flag))) break;
-      const int m0 = (work / n_tiles) * kBM;
+      int m0, n0, gi;
+      const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+      const float* theta = L.theta + (size_t)G.p_off * 5;
+      const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
+      const int n_kb = G.k_pad / kBK;
       float c[4][kNB];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int p = m0 + rg + 32 * rr;
-        if (p < P) coefficients(theta + (size_t)p * 5, sin2w, cref, c[rr]);
+        if (p < G.P) coefficients(theta + (size_t)p * 5, s2w, G.cref, c[rr]);
         else
 #pragma unroll
           for (int b = 0; b < kNB; ++b) c[rr][b] = 0.f;
@@ -321,10 +368,15 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   } else if (warp < kEpiWarp0 + 4) {
     // ------------------------------------------------------------ epilogue
     const int q = warp - kEpiWarp0;  // TMEM lane quarter of this warp
-    int tc = 0;
-    for (int work = blockIdx.x; work < n_work; work += gridDim.x, ++tc) {
+    int tc = -1;
+    FOR_ITEMS(idx) {
+      ++tc;
       if (__any_sync(0xffffffffu, aborted(&abort_flag))) break;
-      const int m0 = (work / n_tiles) * kBM, nt = work % n_tiles, n0 = nt * BN;
+      int m0, n0, gi;
+      const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+      const int bn = GROUPED ? G.bn : BN, nt = n0 / bn, n_rec = G.n_rec, P = G.P;
+      const float2* nb2 = G.nb2;
       const int buf = tc & 1;
       if (!warp_wait(&acc_full[buf], (tc >> 1) & 1, &abort_flag, 256)) {
         give_up();
@@ -336,7 +388,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       dfloat acc = {0.f, 0.f};
       bool infinite = false;  // a +inf term (mu <= 0 with data) is kept apart: TwoSum would make it NaN
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < bn; c0 += 16) {
         // per-column constants first (warp-uniform loads), then the accumulator row
         float2 dj[16];
         if (parts != nullptr) {
@@ -349,7 +401,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         float v[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
         if (musig_out != nullptr && p < P) {  // batched folded spectra (row p)
-          float* row = musig_out + (size_t)p * n_rec;
+          float* row = musig_out + (size_t)(G.p_off + p) * n_rec;
 #pragma unroll
           for (int k = 0; k < 16; ++k)
             if (n0 + c0 + k < n_rec) row[n0 + c0 + k] = v[k];
@@ -369,16 +421,32 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
       if (parts != nullptr && p < P)
-        parts[(size_t)nt * P + p] = infinite ? __longlong_as_double(0x7ff0000000000000LL) : (double)acc.hi + (double)acc.lo;
+        parts[G.parts_off + (long long)nt * P + p] =
+            infinite ? __longlong_as_double(0x7ff0000000000000LL) : (double)acc.hi + (double)acc.lo;
     }
   } else if (warp == kTmaWarp) {
     // ------------------------------------------------------------ TMA producers
     if (lane == 0) {  // R hi (+ lo) tiles into the stage ring
       int g = 0, issued_g = 0;
-      const uint32_t bytes = (uint32_t)(X3 ? 2 : 1) * S::kBB;
-      for (int work = blockIdx.x; work < n_work && !aborted(&abort_flag); work += gridDim.x) {
-        const int n0 = (work % n_tiles) * BN;
-        bool ok = true;
+      bool ok = true;
+      FOR_ITEMS(idx) {
+        if (!ok || aborted(&abort_flag)) break;
+        int m0, n0, gi;
+        const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        const int n_kb = G.k_pad / kBK;
+        const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * kBK * 2);
+        const CUtensorMap* mh = &map_hi;
+        const CUtensorMap* ml = &map_lo;
+        if (GROUPED) {
+          mh = G.map_hi;
+          ml = G.map_lo;
+          if (!((map_fenced[gi >> 5] >> (gi & 31)) & 1u)) {
+            tensormap_acquire(mh);
+            if (X3) tensormap_acquire(ml);
+            map_fenced[gi >> 5] |= 1u << (gi & 31);
+          }
+        }
         for (int kb = 0; kb < n_kb; ++kb, ++g) {
           const int st = g % ST;
           if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
@@ -387,27 +455,34 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             break;
           }
           ptx::mbar_arrive_expect_tx(&r_full[st], bytes);
-          tma_load_2d(b_hi(st), &map_hi, kb * kBK, n0, &r_full[st]);
-          if (X3) tma_load_2d(b_lo(st), &map_lo, kb * kBK, n0, &r_full[st]);
+          tma_load_2d(b_hi(st), mh, kb * kBK, n0, &r_full[st]);
+          if (X3) tma_load_2d(b_lo(st), ml, kb * kBK, n0, &r_full[st]);
           issued_g = g + 1;
         }
-        if (!ok) break;
       }
       // never end with copies in flight
       for (int u = max(0, issued_g - ST); u < issued_g; ++u)
         ptx::mbar_wait(&r_full[u % ST], (u / ST) & 1, nullptr, 100000000ull);
     } else if (lane == 1) {  // coefficient-spectra slices, up to kShatSlots blocks ahead
-      const int total = ((n_work - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x) * n_kb;
-      int issued = 0;
-      for (int g = 0; g < total; ++g) {
-        const int sl = g % kShatSlots;
-        if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
-          give_up();
-          break;
+      int g = 0, issued = 0;
+      bool ok = true;
+      FOR_ITEMS(idx) {
+        if (!ok) break;
+        int m0, n0, gi;
+        const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        const int n_kb = G.k_pad / kBK;
+        for (int kb = 0; kb < n_kb; ++kb, ++g) {
+          const int sl = g % kShatSlots;
+          if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          ptx::mbar_arrive_expect_tx(&s_full[sl], (uint32_t)kShatBytes);
+          ptx::bulk_g2s(shat_s(sl), G.shat_k8 + (size_t)kb * kBK * 2, (uint32_t)kShatBytes, &s_full[sl]);
+          issued = g + 1;
         }
-        ptx::mbar_arrive_expect_tx(&s_full[sl], (uint32_t)kShatBytes);
-        ptx::bulk_g2s(shat_s(sl), shat_k8 + (size_t)(g % n_kb) * kBK * 2, (uint32_t)kShatBytes, &s_full[sl]);
-        issued = g + 1;
       }
       for (int u = max(0, issued - kShatSlots); u < issued; ++u)
         ptx::mbar_wait(&s_full[u % kShatSlots], (u / kShatSlots) & 1, nullptr, 100000000ull);
@@ -415,10 +490,17 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   } else {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-      int g = 0, tc = 0;
+      int g = 0;
       bool issued_any = false;
-      for (int work = blockIdx.x; work < n_work && !aborted(&abort_flag); work += gridDim.x, ++tc) {
+      int tc = -1;
+      FOR_ITEMS(idx) {
+        ++tc;
+        if (aborted(&abort_flag)) break;
+        int m0, n0, gi;
+        const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        const int n_kb = G.k_pad / kBK;
+        const uint32_t idesc = idesc_bf16(kBM, GROUPED ? G.bn : BN);
         const int buf = tc & 1;
         if (!ptx::mbar_wait(&acc_empty[buf], ((tc >> 1) & 1) ^ 1, &abort_flag)) {
           give_up();
@@ -493,22 +575,38 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 template <int BN, bool X3>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(fold_tc_kernel<BN, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(fold_tc_kernel<BN, X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcShape<BN, X3>::kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fold_tc_kernel<BN, X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               TcShape<BN, X3>::kSmem);
 }
 
-template <int BN, bool X3>
-cudaError_t launch_cfg(const srw_ctx* h, const TcMaps* maps, const float* theta, int P, double* parts,
-                       float* musig_out, cudaStream_t s) {
-  using S = TcShape<BN, X3>;
-  const int work = ((P + kBM - 1) / kBM) * ((h->n_rec + BN - 1) / BN);
-  const int grid = work < h->sm_count ? work : h->sm_count;
-  const int bi = BN == 256 ? 1 : 0;
-  fold_tc_kernel<BN, X3><<<grid, kThreads, S::kSmem, s>>>(
-      maps->hi[bi], maps->lo[bi], theta, P, df_from_double(h->sin2w), h->cref,
-      reinterpret_cast<const float4*>(h->d_shat_k8),
-      h->k_pad, h->n_rec, reinterpret_cast<const float2*>(h->d_nb2), parts, musig_out, h->d_status);
+template <int BN, bool X3, bool GROUPED>
+cudaError_t launch_kernel(const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid, cudaStream_t s) {
+  fold_tc_kernel<BN, X3, GROUPED><<<grid, kThreads, TcShape<BN, X3>::kSmem, s>>>(mh, ml, L);
   return cudaGetLastError();
+}
+
+template <bool GROUPED>
+cudaError_t launch_any(int bn_max, bool x3, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid,
+                       cudaStream_t s) {
+  if (bn_max == 256)
+    return x3 ? launch_kernel<256, true, GROUPED>(mh, ml, L, grid, s)
+              : launch_kernel<256, false, GROUPED>(mh, ml, L, grid, s);
+  return x3 ? launch_kernel<128, true, GROUPED>(mh, ml, L, grid, s)
+            : launch_kernel<128, false, GROUPED>(mh, ml, L, grid, s);
+}
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q);
+    if (e == cudaSuccess && p != nullptr && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
 }
 
 }  // namespace
@@ -531,33 +629,35 @@ cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMap* lo) {
+  EncodeTiledFn encode = encode_fn();
+  if (encode == nullptr) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)h->k_pad, (cuuint64_t)h->rec_pad};
+  const cuuint64_t strides[1] = {(cuuint64_t)h->k_pad * 2};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)bn};
+  for (int l = 0; l < 2; ++l) {
+    CUresult r = encode(l ? lo : hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l ? (void*)h->d_rlo : (void*)h->d_rhi, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t tc_prepare(srw_ctx* h) {
   cudaError_t ea = set_attr<256, true>();
   if (ea == cudaSuccess) ea = set_attr<256, false>();
   if (ea == cudaSuccess) ea = set_attr<128, true>();
   if (ea == cudaSuccess) ea = set_attr<128, false>();
   if (ea != cudaSuccess) return ea;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
-  if (e != cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
-  EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
   TcMaps* maps = new (std::nothrow) TcMaps();
   if (!maps) return cudaErrorMemoryAllocation;
-  const cuuint64_t dims[2] = {(cuuint64_t)h->k_pad, (cuuint64_t)h->rec_pad};
-  const cuuint64_t strides[1] = {(cuuint64_t)h->k_pad * 2};
-  const cuuint32_t estr[2] = {1, 1};
   for (int bi = 0; bi < 2; ++bi) {
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)(bi ? 256 : 128)};
-    for (int lo = 0; lo < 2; ++lo) {
-      CUresult r = encode(lo ? &maps->lo[bi] : &maps->hi[bi], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                          lo ? (void*)h->d_rlo : (void*)h->d_rhi, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) {
-        delete maps;
-        return cudaErrorInvalidValue;
-      }
+    const cudaError_t e = tc_encode_maps(h, bi ? 256 : 128, &maps->hi[bi], &maps->lo[bi]);
+    if (e != cudaSuccess) {
+      delete maps;
+      return e;
     }
   }
   h->tmap = maps;
@@ -569,16 +669,61 @@ void tc_release(srw_ctx* h) {
   h->tmap = nullptr;
 }
 
+TcGroup tc_group_of(const srw_ctx* h, int bn) {
+  TcGroup G{};
+  G.map_hi = G.map_lo = nullptr;
+  G.shat_k8 = reinterpret_cast<const float4*>(h->d_shat_k8);
+  G.nb2 = reinterpret_cast<const float2*>(h->d_nb2);
+  G.c_data = h->d_cdata;
+  G.parts_off = 0;
+  G.n_rec = h->n_rec;
+  G.k_pad = h->k_pad;
+  G.P = 0;
+  G.p_off = 0;
+  G.bn = bn;
+  G.n_tiles = (h->n_rec + bn - 1) / bn;
+  const dfloat s2w = df_from_double(h->sin2w);
+  G.sin2w_hi = s2w.hi;
+  G.sin2w_lo = s2w.lo;
+  G.cref = h->cref;
+  return G;
+}
+
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
                            double* parts, cudaStream_t s, int* n_parts, float* musig_out) {
   const TcMaps* maps = static_cast<const TcMaps*>(h->tmap);
   if (!maps) return cudaErrorNotSupported;
-  const bool x3 = precision == SRW_BF16X3;
-  if (n_parts) *n_parts = (h->n_rec + cfg.bn - 1) / cfg.bn;
-  if (cfg.bn == 256) return x3 ? launch_cfg<256, true>(h, maps, theta, P, parts, musig_out, s)
-                               : launch_cfg<256, false>(h, maps, theta, P, parts, musig_out, s);
-  return x3 ? launch_cfg<128, true>(h, maps, theta, P, parts, musig_out, s)
-            : launch_cfg<128, false>(h, maps, theta, P, parts, musig_out, s);
+  const int bn = cfg.bn == 256 ? 256 : 128, bi = bn == 256 ? 1 : 0;
+  TcLaunch L{};
+  L.g0 = tc_group_of(h, bn);
+  L.g0.P = P;
+  L.groups = nullptr;
+  L.items = nullptr;
+  L.n_items = ((P + kBM - 1) / kBM) * L.g0.n_tiles;
+  L.theta = theta;
+  L.parts = parts;
+  L.musig_out = musig_out;
+  L.status = h->d_status;
+  if (n_parts) *n_parts = L.g0.n_tiles;
+  const int grid = L.n_items < h->sm_count ? L.n_items : h->sm_count;
+  return launch_any<false>(bn, precision == SRW_BF16X3, maps->hi[bi], maps->lo[bi], L, grid, s);
 }
+
+cudaError_t launch_fold_tc_group(int bn_max, bool x3, const TcGroup* d_groups, const int4* d_items, int n_slots,
+                                 int n_cta, const float* theta, double* parts, unsigned* status, cudaStream_t s) {
+  if (n_cta < 1) return cudaSuccess;
+  TcLaunch L{};
+  L.groups = d_groups;
+  L.items = d_items;
+  L.n_items = n_slots;
+  L.theta = theta;
+  L.parts = parts;
+  L.musig_out = nullptr;
+  L.status = status;
+  static const CUtensorMap unused{};  // grouped launches read each configuration's maps from its descriptor
+  return launch_any<true>(bn_max == 256 ? 256 : 128, x3, unused, unused, L, n_cta, s);
+}
+
+int tc_max_groups() { return kMaxGroups; }
 
 }  // namespace srw

@@ -533,6 +533,7 @@ srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, i
   if (d_bkg) SRW_CUDA(h, cudaFreeAsync(d_bkg, s), "free bkg");
   SRW_CUDA(h, cudaStreamSynchronize(s), "set_data sync");
   h->has_data = 1;
+  ++h->version;
   return SRW_OK;
 }
 
@@ -812,6 +813,7 @@ srw_status srw_set_reference(srw_handle h, const float* theta_ref) {
   SRW_CUDA(h, launch_reference_fold(h, s), "reference fold");
   if (h->has_data) SRW_CUDA(h, launch_data_ref(h, s), "data kernels");
   SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  ++h->version;
   return SRW_OK;
 }
 

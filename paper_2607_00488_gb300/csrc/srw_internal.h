@@ -1,6 +1,7 @@
 // Internal state and launchers of the srw library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -74,6 +75,30 @@ struct CoefRef {
   float hi[kNB], lo[kNB];
 };
 
+// One detector configuration of a tensor-core fold launch.  A launch over a
+// single handle carries one by value; a grouped launch (several handles, one
+// persistent grid) reads an array of them from device memory.
+struct TcGroup {
+  const CUtensorMap* map_hi;   // R hi / lo maps, box 64 K x bn rows (grouped launches; global memory)
+  const CUtensorMap* map_lo;
+  const float4* shat_k8;       // [k_pad][8] coefficient spectra, k-major
+  const float2* nb2;           // [n_rec] {n_j or -1 where masked, b_j + R W_ref}
+  const double* c_data;        // data constant of -2 ln L (device scalar)
+  long long parts_off;         // partial sums of the group: parts + parts_off, [n_tiles][P]
+  int n_rec, k_pad, P, p_off;  // p_off: first point of the group in the launch's theta / out
+  int bn, n_tiles;             // rec tile width (128 or 256) and number of rec tiles
+  float sin2w_hi, sin2w_lo;
+  CoefRef cref;
+};
+
+// Where the per-tile partial sums of one configuration live, for the final
+// reduction of a grouped call.
+struct GroupPart {
+  long long parts_off;
+  int n_parts, P, p_off, pad;
+  const double* c_data;
+};
+
 // Tile configuration of the batched fold.
 struct FoldConfig {
   int kind;      // 0 = SIMT FP32, 1 = tcgen05
@@ -93,6 +118,7 @@ struct srw_ctx {
   double t_min = 1e-3, sin2w = 0.23121, f_tau = 0.5, exposure = 0, lambda = 0, kappa = 0;
   int has_esm_input = 0;
   int has_data = 0;
+  unsigned long long version = 0;  // bumped when data or the reference point change
   size_t device_bytes = 0;
 
   // model tables
@@ -199,5 +225,19 @@ FoldConfig tc_config(int i);
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
                            double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr);
 cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s);
+int tc_max_groups();
+// Descriptor of handle h as a configuration with rec tile bn (maps left null).
+TcGroup tc_group_of(const srw_ctx* h, int bn);
+// Tensor maps of h's BF16 hi / lo response with a box of 64 K x bn rows.
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMap* lo);
+// One persistent launch of n_cta CTAs over several configurations.  Slot
+// k * n_cta + b of items (n_slots in all) is CTA b's k-th item {group, m0,
+// n0, 0}; a group < 0 ends that CTA's list.  bn_max (128 or 256) bounds every
+// group's bn.
+cudaError_t launch_fold_tc_group(int bn_max, bool x3, const TcGroup* d_groups, const int4* d_items, int n_slots,
+                                 int n_cta, const float* theta, double* parts, unsigned* status, cudaStream_t s);
+// -2 ln L of every point of a grouped call from its per-tile partial sums.
+cudaError_t launch_group_reduce(const GroupPart* d_gparts, int n_groups, int max_P, const double* parts,
+                                double* out, unsigned* status, cudaStream_t s);
 
 }  // namespace srw

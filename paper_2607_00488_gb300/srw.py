@@ -25,7 +25,9 @@ PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3}
 # Entry points declared in include/srw.h (checked by the test-suite).
 EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "srw_loglik", "srw_loglik_points", "srw_get_basis",
            "srw_autotune", "srw_info", "srw_set_reference", "srw_profile", "srw_profile_read", "srw_last_error", "srw_status_string",
-           "srw_destroy", "srw_loglik_point_noalloc", "srw_noalloc_last_error")
+           "srw_destroy", "srw_loglik_point_noalloc", "srw_noalloc_last_error", "srw_group_create", "srw_group_loglik",
+           "srw_group_autotune", "srw_group_set_schedule", "srw_group_schedule", "srw_group_profile", "srw_group_profile_read",
+           "srw_group_last_error", "srw_group_destroy")
 
 
 class SrwError(RuntimeError):
@@ -87,8 +89,19 @@ def lib():
         L.srw_loglik_point_noalloc.argtypes = [vp, ip, ip, vp, vp, vp, vp, vp, vp]
         L.srw_noalloc_last_error.argtypes = []
         L.srw_noalloc_last_error.restype = ctypes.c_char_p
+        ipp = ctypes.POINTER(ctypes.c_int)
+        L.srw_group_create.argtypes = [vp, ip, vp, ctypes.POINTER(vp)]
+        L.srw_group_loglik.argtypes = [vp, vp, vp, ip, ip, vp]
+        L.srw_group_autotune.argtypes = [vp, ip, vp, ipp]
+        L.srw_group_set_schedule.argtypes = [vp, ip, ip]
+        L.srw_group_schedule.argtypes = [vp, ip, ipp, ipp, ipp, ipp, ipp]
+        L.srw_group_profile.argtypes = [vp, ip]
+        L.srw_group_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.srw_group_last_error.argtypes = [vp]
+        L.srw_group_last_error.restype = ctypes.c_char_p
+        L.srw_group_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name not in ("srw_last_error", "srw_status_string", "srw_noalloc_last_error"):
+            if name not in ("srw_last_error", "srw_status_string", "srw_noalloc_last_error", "srw_group_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -278,6 +291,73 @@ def srw_loglik_point_noalloc(R, W, counts, out, bkg=None, mask=None, stream=None
     return out
 
 
+def _gcheck(status, g):
+    if status != SRW_OK:
+        msg = (lib().srw_group_last_error(g) if g else lib().srw_status_string(status)).decode(errors="replace")
+        raise SrwError(status, msg)
+
+
+def srw_group_create(handles, P):
+    """Group handles with P[g] points each (see srw_group_create in include/srw.h)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    pv = np.ascontiguousarray(P, dtype=np.int32)
+    g = ctypes.c_void_p()
+    _gcheck(lib().srw_group_create(hs, n, pv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(g)), None)
+    return g
+
+
+def srw_group_loglik(g, theta, precision=SRW_BF16X3, out=None, stream=None):
+    """-2 ln L of all points of all configurations (theta: sum(P) x 5, concatenated)."""
+    if _is_device(theta):
+        _gcheck(lib().srw_group_loglik(g, ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       SRW_DEVICE, int(precision), _stream(stream)), g)
+        return out
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
+    res = np.empty(th.shape[0], dtype=np.float64) if out is None else out
+    st = lib().srw_group_loglik(g, th.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
+                                SRW_HOST, int(precision), None)
+    if st == SRW_EDOMAIN:
+        return res
+    _gcheck(st, g)
+    return res
+
+
+def srw_group_autotune(g, precision, stream=None):
+    chosen = ctypes.c_int(-1)
+    _gcheck(lib().srw_group_autotune(g, int(precision), _stream(stream) if stream is not None else None,
+                                     ctypes.byref(chosen)), g)
+    return chosen.value
+
+
+def srw_group_set_schedule(g, precision, candidate):
+    _gcheck(lib().srw_group_set_schedule(g, int(precision), int(candidate)), g)
+
+
+def srw_group_schedule(g, precision, n_groups):
+    bn_max, n_items, n_cta, cand = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    bn = (ctypes.c_int * n_groups)()
+    _gcheck(lib().srw_group_schedule(g, int(precision), ctypes.byref(bn_max), bn, ctypes.byref(n_items),
+                                     ctypes.byref(n_cta), ctypes.byref(cand)), g)
+    return {"bn_max": bn_max.value, "bn": list(bn), "n_items": n_items.value, "n_cta": n_cta.value,
+            "candidate": cand.value}
+
+
+def srw_group_profile(g, enable):
+    _gcheck(lib().srw_group_profile(g, 1 if enable else 0), g)
+
+
+def srw_group_profile_read(g):
+    ms = ctypes.c_float()
+    _gcheck(lib().srw_group_profile_read(g, ctypes.byref(ms)), g)
+    return ms.value
+
+
+def srw_group_destroy(g):
+    if g:
+        lib().srw_group_destroy(g)
+
+
 def srw_last_error(h):
     return lib().srw_last_error(h).decode(errors="replace")
 
@@ -322,6 +402,55 @@ class Likelihood:
     def close(self):
         if self.handle:
             srw_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GroupedLikelihood:
+    """Several configurations (``Likelihood`` objects) evaluated in one
+    persistent launch; ``P[g]`` points for configuration g."""
+
+    def __init__(self, likelihoods, P):
+        self.members = list(likelihoods)  # the group does not own the handles; keep them alive
+        self.P = [int(p) for p in P]
+        self.handle = srw_group_create([lk.handle for lk in self.members], self.P)
+
+    @property
+    def offsets(self):
+        return np.concatenate([[0], np.cumsum(self.P)]).astype(np.int64)
+
+    def loglik(self, theta, precision=SRW_BF16X3, out=None, stream=None):
+        return srw_group_loglik(self.handle, theta, precision, out, stream)
+
+    def autotune(self, precision, stream=None):
+        return srw_group_autotune(self.handle, precision, stream)
+
+    def set_schedule(self, precision, candidate):
+        srw_group_set_schedule(self.handle, precision, candidate)
+
+    def schedule(self, precision):
+        return srw_group_schedule(self.handle, precision, len(self.members))
+
+    def profile(self, enable):
+        srw_group_profile(self.handle, enable)
+
+    def profile_read(self):
+        return srw_group_profile_read(self.handle)
+
+    def close(self):
+        if self.handle:
+            srw_group_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

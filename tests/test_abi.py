@@ -73,3 +73,10 @@ def test_create_rejects_invalid_arguments(srw, bad):
     with pytest.raises(srw.SrwError) as ei:
         srw.srw_create(a["t_edges"], a["n_rec"], a["sources"], r, a["exposure"])
     assert ei.value.status == 1  # SRW_EINVAL, raised before any device call
+
+
+@pytest.mark.parametrize("handles,P", [([], []), ([None], [4]), ([None, None], [1, 2])])
+def test_group_create_rejects_invalid_arguments(srw, handles, P):
+    with pytest.raises(srw.SrwError) as ei:
+        srw.srw_group_create(handles, P)
+    assert ei.value.status == 1  # SRW_EINVAL, raised before any device call

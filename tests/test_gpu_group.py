@@ -1,0 +1,261 @@
+"""GPU parity of the grouped evaluation (several detector configurations in
+one persistent fold launch) through the C ABI.
+
+* The grouped launch runs, per configuration, the same arithmetic as that
+  configuration's own batched fold: with equal tile widths the values are
+  bit-identical to srw_loglik on the member handle; other tile widths change
+  only the grouping of the FP64 partial sums (relative 1e-9).
+* Against the FP64 oracle, every sampled point satisfies the policy of the
+  single-configuration tests: |d| <= tol + 2 B with the measured budget
+  B = 2 sum_j |1 - n_j/mu_j| |dmu_j| (dmu_j from the same fold's spectra), and
+  |d| <= tol in the fit region.  The fit region shrinks with the exposure E
+  as a confidence region does: |eps| <= 0.02 sqrt(1e5 / E) and
+  mu_hat <= 0.5 (1e5 / E)^(1/4) (the magnetic-moment rate goes as mu_hat^2),
+  i.e. the region of the 1e5-event tests scaled to equal Delta(-2 ln L).
+  Outside it the model is far from the data (|mu - n| >> sqrt(mu)) and
+  FP32-level per-bin errors alone move -2 ln L by more than 1e-4.  The BF16
+  hi+lo split keeps ~16 significant bits of R and of W - W_ref, an error that
+  grows with the exposure like sqrt(E) at fixed Delta(-2 ln L); its absolute
+  bar applies up to 1e5 events, the budget bound everywhere.
+* Ragged sizes: configurations with 0, 1 and 129 points, rec-bin counts that
+  are not multiples of the tile width, true-bin counts that are not multiples
+  of the K block.
+* The full 64-configuration workload (N_T 512-8192, N_rec 256-4096, 256-4096
+  points each) against the member paths and sampled oracle points.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 2: 1e-3}  # SRW_FP32, SRW_BF16X3 in the fit region
+
+
+@pytest.fixture(scope="module")
+def srw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2607_00488_gb300 as pkg
+    return pkg
+
+
+def near_sm(n, seed, exposure=1e5):
+    """Fit-region points around the SM reference for a configuration of the
+    given exposure (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    s = 1e5 / exposure
+    th = np.zeros((n, 5), np.float32)
+    th[:, :4] = rng.uniform(-0.02, 0.02, (n, 4)) * np.sqrt(s)
+    th[:, 4] = rng.uniform(0.0, 0.5, n) * s ** 0.25
+    return th
+
+
+class Member:
+    def __init__(self, srw, wl, counts, P, seed):
+        self.wl, self.counts, self.P = wl, counts, P
+        self.lk = srw.Likelihood(wl, counts)
+        self.ref = None
+        n_fit = min(P, 4)
+        box = workloads.theta_box(P, 500 + seed)
+        box[:n_fit] = near_sm(n_fit, 700 + seed, wl["exposure"])
+        self.theta = box.reshape(P, 5)
+        self.n_fit = n_fit
+
+    def oracle(self):
+        if self.ref is None:
+            self.ref = O.OracleModel.from_workload(self.wl)
+            self.ref.set_data(self.counts, self.wl["bkg"])
+        return self.ref
+
+
+def _oracle_counts(wl):
+    m = O.OracleModel.from_workload(wl)
+    m.set_data(np.zeros(wl["R"].shape[0]), wl["bkg"])
+    return workloads.poisson_counts(m.mu(np.zeros(5)), 0), m
+
+
+@pytest.fixture(scope="module")
+def small(srw):
+    """Ten scaled-down uneven configurations and the 7Be line, with ragged
+    point counts (0, 1, 129) among them."""
+    gw = workloads.uneven_groups_workload(n_groups=10, seed=4, scale=0.08)
+    wls = [workloads.uneven_group_inputs(gw, g) for g in range(10)] + [workloads.be7_line_workload()]
+    P = [spec["p"] for spec in gw["groups"]] + [16]
+    P[2], P[5], P[7] = 1, 0, 129
+    members = []
+    for i, wl in enumerate(wls):
+        counts, model = _oracle_counts(wl)
+        m = Member(srw, wl, counts, P[i], i)
+        model.set_data(counts, wl["bkg"])
+        m.ref = model
+        members.append(m)
+    grp = srw.GroupedLikelihood([m.lk for m in members], P)
+    yield members, grp
+    grp.close()
+    for m in members:
+        m.lk.close()
+
+
+def _theta_all(members):
+    return np.concatenate([m.theta for m in members if m.P > 0]).astype(np.float32)
+
+
+def _split(values, members):
+    out, off = [], 0
+    for m in members:
+        out.append(values[off:off + m.P])
+        off += m.P
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_group_equals_member_folds_bitwise(srw, small, prec):
+    members, grp = small
+    grp.set_schedule(prec, 0)  # every configuration with 256-bin tiles, as the members' default
+    got = _split(grp.loglik(_theta_all(members), prec), members)
+    for m, g in zip(members, got):
+        if m.P == 0:
+            continue
+        want = m.lk.loglik(m.theta, prec)
+        assert np.array_equal(g, want), (m.wl["name"], np.max(np.abs(g - want)))
+
+
+def test_group_fp32_equals_member_folds(srw, small):
+    members, grp = small
+    got = _split(grp.loglik(_theta_all(members), 0), members)
+    for m, g in zip(members, got):
+        if m.P == 0:
+            continue
+        if m.P == 1:  # the member runs its single-point (GEMV) path here; the oracle test covers it
+            continue
+        assert np.array_equal(g, m.lk.loglik(m.theta, 0)), m.wl["name"]  # same SIMT fold
+
+
+@pytest.mark.parametrize("cand", [1, 2])
+def test_group_schedules_agree(srw, small, cand):
+    members, grp = small
+    th = _theta_all(members)
+    grp.set_schedule(2, 0)
+    base = grp.loglik(th, 2)
+    grp.set_schedule(2, cand)
+    got = grp.loglik(th, 2)
+    sch = grp.schedule(2)
+    assert sch["candidate"] == cand
+    if cand == 2:
+        assert sch["bn_max"] == 128 and set(sch["bn"]) == {128}
+    np.testing.assert_allclose(got, base, rtol=1e-9, atol=1e-9)
+    grp.set_schedule(2, 0)
+
+
+def _budget(m, th, mu_sig_gpu):
+    ref = m.oracle()
+    mu = ref.mu(th.astype(np.float64))
+    dmu = np.asarray(mu_sig_gpu, np.float64) - ref.mu_sig(th.astype(np.float64))
+    on = mu > 0
+    return 2.0 * np.sum(np.abs(1.0 - m.counts[on] / mu[on]) * np.abs(dmu[on]))
+
+
+def _check_vs_oracle(srw, members, got_by_member, prec, idx_fn):
+    worst = []
+    for m, g in zip(members, got_by_member):
+        if m.P == 0:
+            continue
+        for i in idx_fn(m):
+            th = m.theta[i]
+            want = m.oracle().neg2lnl(th.astype(np.float64))
+            d = abs(g[i] - want)
+            musig = m.lk.spectrum_batch(th[None, :], prec)[0]
+            b = _budget(m, th, musig)
+            fit = i < m.n_fit
+            worst.append((d, b, fit, m.wl["exposure"], m.wl["name"], i))
+            assert d <= TOL[prec] + 2.0 * b, (m.wl["name"], i, d, b)
+            if fit and (prec == 0 or m.wl["exposure"] <= 1e5):
+                assert d <= TOL[prec], (m.wl["name"], i, d, b)
+    return worst
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_group_vs_oracle(srw, small, prec):
+    members, grp = small
+    grp.set_schedule(2, 1)
+    got = _split(grp.loglik(_theta_all(members), prec), members)
+    worst = _check_vs_oracle(srw, members, got, prec, lambda m: sorted({0, min(1, m.P - 1), m.P - 1}))
+    worst.sort(reverse=True)
+    print("largest |d| (d, budget, fit, exposure, config, point):", worst[:3])
+
+
+def test_group_picks_up_reference_and_data_changes(srw, small):
+    members, grp = small
+    th = _theta_all(members)
+    grp.set_schedule(2, 0)
+    m = members[0]
+    m.lk.set_reference(m.theta[0])
+    try:
+        got = _split(grp.loglik(th, 2), members)[0]
+        assert np.array_equal(got, m.lk.loglik(m.theta, 2))
+    finally:
+        m.lk.set_reference(np.zeros(5, np.float32))
+    got = _split(grp.loglik(th, 2), members)[0]
+    assert np.array_equal(got, m.lk.loglik(m.theta, 2))
+
+
+def test_group_device_pointers_on_torch_stream(srw, small):
+    members, grp = small
+    th = _theta_all(members)
+    want = grp.loglik(th, 2)
+    th_d = torch.from_numpy(th).cuda()
+    out = torch.empty(th.shape[0], dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        grp.loglik(th_d, 2, out=out, stream=s)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_group_autotune_returns_a_candidate(srw, small):
+    members, grp = small
+    c = grp.autotune(2)
+    assert c in (0, 1, 2)
+    assert grp.schedule(2)["candidate"] == c
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def uneven64(srw):
+    gw = workloads.uneven_groups_workload()
+    counts = workloads.load_group_counts(gw)
+    members = []
+    for g, spec in enumerate(gw["groups"]):
+        wl = workloads.uneven_group_inputs(gw, g)
+        members.append(Member(srw, wl, counts[g], spec["p"], 100 + g))
+    grp = srw.GroupedLikelihood([m.lk for m in members], [m.P for m in members])
+    yield members, grp
+    grp.close()
+    for m in members:
+        m.lk.close()
+
+
+def test_uneven64_equals_member_folds(srw, uneven64):
+    members, grp = uneven64
+    grp.set_schedule(2, 0)
+    got = _split(grp.loglik(_theta_all(members), 2), members)
+    for m, g in zip(members, got):
+        assert np.array_equal(g, m.lk.loglik(m.theta, 2)), m.wl["name"]
+
+
+def test_uneven64_sampled_vs_oracle(srw, uneven64):
+    members, grp = uneven64
+    grp.set_schedule(2, 1)
+    got = _split(grp.loglik(_theta_all(members), 2), members)
+    # one fit-region point and one box point in every fourth configuration
+    sub = [(m, g) for k, (m, g) in enumerate(zip(members, got)) if k % 4 == 0]
+    worst = _check_vs_oracle(srw, [m for m, _ in sub], [g for _, g in sub], 2, lambda m: [0, m.P - 1])
+    worst.sort(reverse=True)
+    print("largest |d| (d, budget, fit, exposure, config, point):", worst[:3])

@@ -19,6 +19,9 @@ from .solar import (  # noqa: F401
     solar_set_workload,
     batched_scan_workload,
     uneven_groups_workload,
+    uneven_group_inputs,
+    group_counts_path,
+    load_group_counts,
     theta_box,
     poisson_counts,
     load_counts,

@@ -298,6 +298,20 @@ def counts_path(name):
     return os.path.join(_DATA_DIR, name + "_counts.txt")
 
 
+def group_counts_path(name):
+    return os.path.join(_DATA_DIR, name + "_counts.txt.gz")
+
+
+def load_group_counts(groups_wl):
+    """Stored pseudo-data of every configuration of a grouped workload (one
+    array per configuration, written by the oracle's data script)."""
+    flat = np.loadtxt(group_counts_path(groups_wl["name"]), dtype=np.float64).reshape(-1)
+    sizes = [g["n_rec"] for g in groups_wl["groups"]]
+    if flat.size != sum(sizes):
+        raise ValueError("stored grouped counts do not match the workload")
+    return np.split(flat, np.cumsum(sizes)[:-1])
+
+
 def load_counts(name):
     """Stored pseudo-data counts for a workload (written once by the oracle's
     data script from the SM expectation, Poisson seed 0)."""
