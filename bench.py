@@ -8,7 +8,7 @@ response fold, the fused Poisson epilogue and the FP64 per-point reduction,
 replayed from a captured CUDA graph.  Inputs are resident in HBM; L2 is
 flushed (a 256 MiB write) before every timed step.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|bf16|fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16x3|bf16x3|bf16|fp32]
     python bench.py --impl reference ...     # the FP64 oracle on the host cores
 
 Under torchrun each rank evaluates its own batch (weak scaling); the step
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srw", choices=["srw", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "bf16", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp16x3", "bf16x3", "bf16", "fp32"])
     ap.add_argument("--points", type=int, default=65536)
     ap.add_argument("--cpu-sample", type=int, default=12, help="theta points for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--grouped-only", action="store_true",
                     help="only the grouped measurement (for profiling its launch)")
     return ap.parse_args()
+
+
+# tensor-core products per useful flop, and the peak each precision is held to
+PRODUCTS = {0: 1, 1: 1, 2: 3, 3: 3}  # SRW_FP32, SRW_BF16, SRW_BF16X3, SRW_FP16X3
+PEAK_NOTE = {0: "152 SMs x 128 FP32 lanes x 2 flop x max clock", 1: "bf16 burst",
+             2: "bf16 burst / 3 products", 3: "bf16 burst (= dense fp16 rate) / 3 products"}
+DTYPE = {0: "f32", 1: "bf16", 2: "bf16", 3: "f16"}
 
 
 def dist_env():
@@ -251,16 +258,16 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
         fold_ms.append(grp.profile_read())
     grp.profile(False)
     fold_s = statistics.mean(fold_ms) * 1e-3
-    peak = peaks["bf16_tflops"] / (3.0 if prec == srw.SRW_BF16X3 else 1.0)
+    peak = peaks["bf16_tflops"] / PRODUCTS[prec]
     n_pts = int(th.shape[0])
     res = {
         "workload": gw["name"], "configurations": len(P), "points": n_pts,
         "evals_s": n_pts * args.steps / (sum(step_ms) * 1e-3), "ms_per_step": statistics.mean(step_ms),
-        "launches_per_step": 2,
+        "launches_per_step": 3 if prec == srw.SRW_FP16X3 else 2,
         "roofline": {"bound": "tensor", "achieved": useful / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": useful / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel (grouped)",
                      "useful_tflop_per_launch": useful / 1e12, "fold_ms": statistics.mean(fold_ms),
-                     "peak_source": "%s (bf16 burst%s)" % (peak_src, " / 3 products" if prec == srw.SRW_BF16X3 else "")},
+                     "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec])},
         "schedule": {"candidate": cand, "bn_max": sched["bn_max"], "items": sched["n_items"], "ctas": sched["n_cta"],
                      "configs_bn128": sum(1 for b in sched["bn"] if b == 128)},
     }
@@ -294,7 +301,7 @@ def main():
     if args.grouped_only:
         stream = torch.cuda.current_stream(dev)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-        prec = srw.PRECISIONS["bf16x3" if args.precision == "auto" else args.precision]
+        prec = srw.PRECISIONS["fp16x3" if args.precision == "auto" else args.precision]
         peaks, peak_src = measured_peaks()
         print(json.dumps(grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)))
         return 0
@@ -307,7 +314,7 @@ def main():
     info = lk.info()
     prec_name = args.precision
     if prec_name == "auto":
-        prec_name = "bf16x3" if info["tensor_path"] else "fp32"
+        prec_name = "fp16x3" if info["tensor_path"] else "fp32"
     prec = srw.PRECISIONS[prec_name]
     if prec != srw.SRW_FP32:
         srw.srw_autotune(h, P, prec)
@@ -358,19 +365,44 @@ def main():
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, kernel_file, tag = "alu", "paper_2607_00488_gb300/csrc/fold_simt.cu", "fold_simt_kernel"
     else:
-        # useful flops against the effective peak of the precision: one BF16
-        # product per useful flop (bf16), three for the hi+lo split (bf16x3)
-        peak = peaks["bf16_tflops"] / (3.0 if prec == srw.SRW_BF16X3 else 1.0)
+        # useful flops against the effective peak of the precision: one
+        # tensor-core product per useful flop (bf16), three for the hi+lo
+        # splits (bf16x3, fp16x3; dense FP16 and BF16 run at the same rate)
+        peak = peaks["bf16_tflops"] / PRODUCTS[prec]
         bound, kernel_file, tag = "tensor", "paper_2607_00488_gb300/csrc/fold_tc.cu", "fold_tc_kernel"
     achieved = useful / fold_avg_s / 1e12
-    executed = useful * (3 if prec == srw.SRW_BF16X3 else 1)
+    executed = useful * PRODUCTS[prec]
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(kernel_file, tag + ":" + prec_name),
                 "kernel": tag,
-                "peak_source": "%s (%s)" % (peak_src, {srw.SRW_FP32: "152 SMs x 128 FP32 lanes x 2 flop x max clock",
-                                                        srw.SRW_BF16: "bf16 burst",
-                                                        srw.SRW_BF16X3: "bf16 burst / 3 products"}[prec]),
+                "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec]),
                 "executed_tflops": executed / fold_avg_s / 1e12, "fold_ms": statistics.mean(fold_ms)}
+
+    # the other tensor-core split timed the same way (reported beside the headline)
+    alt = {}
+    alt_prec = {srw.SRW_FP16X3: srw.SRW_BF16X3, srw.SRW_BF16X3: srw.SRW_FP16X3}.get(prec)
+    if alt_prec is not None:
+        srw.srw_autotune(h, P, alt_prec)
+        out_alt = torch.empty(P, dtype=torch.float64, device=dev)
+        srw.srw_profile(h, True)
+        for _ in range(args.warmup):
+            flush.add_(1.0)
+            lk.loglik(th, alt_prec, out=out_alt, stream=stream)
+        a_ms, a_fold = [], []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            e0.record(stream)
+            lk.loglik(th, alt_prec, out=out_alt, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            a_ms.append(e0.elapsed_time(e1))
+            a_fold.append(srw.srw_profile_read(h))
+        srw.srw_profile(h, False)
+        a_fold_s = statistics.mean(a_fold) * 1e-3
+        alt_name = {v: k for k, v in srw.PRECISIONS.items()}[alt_prec]
+        alt = {"precision": alt_name, "value": P * args.steps / (sum(a_ms) * 1e-3), "ms_per_step": statistics.mean(a_ms),
+               "fold_ms": statistics.mean(a_fold),
+               "frac": useful / a_fold_s / 1e12 / (peaks["bf16_tflops"] / PRODUCTS[alt_prec])}
 
     # e2e: the public call with host buffers (H2D theta, D2H result inside the timing)
     th_host = np.ascontiguousarray(wl["theta"])
@@ -416,13 +448,14 @@ def main():
     gpu_vals = out.cpu().numpy()
     n_fit = 8
     gpu_fit = lk.loglik(fit_region_points(n_fit), prec)
+    alt_fit = lk.loglik(fit_region_points(n_fit), alt_prec) if alt else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if prec != srw.SRW_FP32 else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
         "config": workload_config(P, prec_name), "roofline": roofline, "e2e": e2e,
-        "gpu_launches": 2 * args.steps, "single_point_fp32": single,
+        "gpu_launches": (3 if prec == srw.SRW_FP16X3 else 2) * args.steps, "single_point_fp32": single,
     }
     if clk:
         line["clocks"] = clk
@@ -435,9 +468,13 @@ def main():
         line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%d evenly spaced theta of the %d-point batch, FP64 numpy, 1 thread"
                                           % (len(idx), P)}
+        if alt:
+            alt["fit_region_max_abs_d"] = max(abs(g - v) for g, v in zip(alt_fit, fit))
         line["parity"] = {"fit_region_n": len(dfit), "fit_region_max_abs_d": max(dfit),
                           "box_sample_n": len(d), "box_sample_max_abs_d": max(d),
                           "box_sample_median_abs_d": statistics.median(d)}
+    if alt:
+        line["other_split"] = alt
     if rank == 0:
         print(json.dumps(line))
     lk.close()

@@ -72,9 +72,17 @@ typedef enum { SRW_HOST = 0, SRW_DEVICE = 1 } srw_where;
  *                tensor cores, FP32 accumulation in tensor memory.
  *   SRW_BF16X3 : both operands split x = hi + lo (BF16 each, round to
  *                nearest even); the three products hi*hi + hi*lo + lo*hi
- *                accumulate in FP32 on the tensor cores.
+ *                accumulate in FP32 on the tensor cores.  The split keeps
+ *                about 16 significant bits of each operand.
+ *   SRW_FP16X3 : the same three products with FP16 hi and lo (about 22
+ *                significant bits), each operand first scaled by an exact
+ *                power of two into FP16 range: every row of R by its own
+ *                factor (fixed at srw_create), the weighted-spectrum
+ *                deviations of each point by a factor from a bound on their
+ *                size; the epilogue divides both out exactly.  Same tensor-
+ *                core work as SRW_BF16X3.
  * The -2lnL bin reduction accumulates in FP64 for every precision. */
-typedef enum { SRW_FP32 = 0, SRW_BF16 = 1, SRW_BF16X3 = 2 } srw_precision;
+typedef enum { SRW_FP32 = 0, SRW_BF16 = 1, SRW_BF16X3 = 2, SRW_FP16X3 = 3 } srw_precision;
 
 /* Recoil binning (Sec. III.A).  The lower integration limit of every bin is
  * max(T_lo, t_min): t_min > 0 is the analysis threshold that regulates the

@@ -13,6 +13,7 @@ from .srw import (  # noqa: F401
     SRW_BF16X3,
     SRW_DEVICE,
     SRW_EDOMAIN,
+    SRW_FP16X3,
     SRW_FP32,
     SRW_HOST,
     GroupedLikelihood,

@@ -27,7 +27,12 @@
 // R W_ref enters the epilogue with the background), so the BF16 rounding
 // errors scale with the distance of theta from the reference.
 // Precision: SRW_BF16 issues hi*hi; SRW_BF16X3 issues hi*hi + hi*lo + lo*hi,
-// all accumulating in FP32 in TMEM.  The accumulator is double-buffered
+// all accumulating in FP32 in TMEM.  SRW_FP16X3 issues the same three
+// products on FP16 halves (11 significant bits each instead of 8): every row
+// j of R is stored scaled by r_j and every point's W - W_ref by s_p, exact
+// powers of two that bring the largest element to [2^13, 2^14) (FP16 keeps
+// full precision from 2^-14 up to 65504); the epilogue multiplies the
+// accumulator by 1 / (s_p r_j), which is exact.  The accumulator is double-buffered
 // (2 x BN columns) so the epilogue of one tile overlaps the next tile's MMAs.
 //
 // Grouped launches (several detector configurations with their own binning,
@@ -60,7 +65,8 @@ constexpr int kShatBytes = kBK * kNB * 4;  // coefficient spectra of one K block
 constexpr int kShatSlots = 4;              // depth of the coefficient-spectra ring
 
 struct TcMaps {
-  CUtensorMap hi[2], lo[2];  // index 0: box rows 128, 1: box rows 256
+  CUtensorMap hi[2], lo[2];      // BF16 split; index 0: box rows 128, 1: box rows 256
+  CUtensorMap hi16[2], lo16[2];  // FP16 split of the row-scaled R
 };
 
 // ---------------------------------------------------------------- tcgen05 PTX
@@ -126,14 +132,45 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor, kind::f16, FP32 accumulator, both operands K-major
+// and of one type: BF16 x BF16 (operand format 1) or F16 x F16 (format 0).
+__host__ __device__ constexpr uint32_t idesc_f16kind(int m, int n, bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+  const __half2 v = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// hi / lo halves of two values: hi = round(x), lo = round(x - hi), packed in pairs.
+template <bool F16>
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  if (F16) {
+    hi = pack_f16x2(a, b);
+    const __half2 v = *reinterpret_cast<const __half2*>(&hi);
+    lo = pack_f16x2(a - __low2float(v), b - __high2float(v));
+  } else {
+    hi = pack_bf16x2(a, b);
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+    lo = pack_bf16x2(a - __low2float(v), b - __high2float(v));
+  }
+}
+
+// Power of two s with s * bound in [2^13, 2^14): the FP16 scale of values
+// bounded by `bound` in magnitude (1 if bound is 0).
+__device__ __forceinline__ float pow2_scale(float bound) {
+  if (!(bound > 0.f)) return 1.f;
+  int e;
+  frexpf(bound, &e);  // bound = m 2^e, m in [0.5, 1)
+  e = e < -100 ? -100 : (e > 100 ? 100 : e);
+  return ldexpf(1.f, 14 - e);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -184,6 +221,7 @@ struct TcLaunch {
   const int4* items;           // grouped: slot k * gridDim.x + b = {group, m0, n0, 0}, CTA b's k-th item
   int n_items;                 // single: m_tiles x n_tiles; grouped: slots
   const float* theta;          // [points][5]; a group's points start at p_off
+  const float* wscale;         // SRW_FP16X3: per-point scales s_p (indexed like theta)
   double* parts;
   float* musig_out;            // single configuration only: [P][n_rec] folded deviations
   unsigned* status;
@@ -228,7 +266,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
 // TMEM accumulators.  In a grouped launch each configuration's tile width
 // bn <= BN is a runtime value (TMA box, MMA N, epilogue columns); a single
 // configuration uses bn = BN.
-template <int BN, bool X3, bool GROUPED>
+template <int BN, bool X3, bool GROUPED, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
 fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcLaunch L) {
   using S = TcShape<BN, X3>;
@@ -301,14 +339,18 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const float* theta = L.theta + (size_t)G.p_off * 5;
       const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
       const int n_kb = G.k_pad / kBK;
-      float c[4][kNB];
+      float c[4][kNB], sc[4];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int p = m0 + rg + 32 * rr;
-        if (p < G.P) coefficients(theta + (size_t)p * 5, s2w, G.cref, c[rr]);
-        else
+        sc[rr] = 1.f;
+        if (p < G.P) {
+          coefficients(theta + (size_t)p * 5, s2w, G.cref, c[rr]);
+          if (F16) sc[rr] = L.wscale[(size_t)G.p_off + p];
+        } else {
 #pragma unroll
           for (int b = 0; b < kNB; ++b) c[rr][b] = 0.f;
+        }
       }
       bool ok = true;
       for (int kb = 0; kb < n_kb; ++kb, ++g) {
@@ -340,11 +382,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           }
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
-            h[rr][q] = pack_bf16x2(w[rr][0], w[rr][1]);
-            if (X3) {
-              const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&h[rr][q]);
-              l[rr][q] = pack_bf16x2(w[rr][0] - __low2float(v), w[rr][1] - __high2float(v));
-            }
+            if (X3) split2<F16>(w[rr][0] * sc[rr], w[rr][1] * sc[rr], h[rr][q], l[rr][q]);
+            else h[rr][q] = pack_bf16x2(w[rr][0], w[rr][1]);
           }
         }
         // the four rows share the swizzle phase (row & 7)
@@ -385,6 +424,9 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       tc_fence_after();
       const int p = m0 + q * 32 + lane;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+      const float* rinv = G.rinv;
+      float sinv = 1.f;  // 1 / s_p (exact: s_p is a power of two)
+      if (F16 && p < P) sinv = 1.f / L.wscale[(size_t)G.p_off + p];
       dfloat acc = {0.f, 0.f};
       bool infinite = false;  // a +inf term (mu <= 0 with data) is kept apart: TwoSum would make it NaN
 #pragma unroll 1
@@ -400,6 +442,13 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         }
         float v[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
+        if (F16) {  // undo the power-of-two scales of both operands
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int j = n0 + c0 + k;
+            v[k] *= sinv * (j < n_rec ? __ldg(rinv + j) : 0.f);
+          }
+        }
         if (musig_out != nullptr && p < P) {  // batched folded spectra (row p)
           float* row = musig_out + (size_t)(G.p_off + p) * n_rec;
 #pragma unroll
@@ -433,7 +482,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         if (!ok || aborted(&abort_flag)) break;
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
-      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
         const int n_kb = G.k_pad / kBK;
         const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * kBK * 2);
         const CUtensorMap* mh = &map_hi;
@@ -470,7 +519,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         if (!ok) break;
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
-      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
         const int n_kb = G.k_pad / kBK;
         for (int kb = 0; kb < n_kb; ++kb, ++g) {
           const int sl = g % kShatSlots;
@@ -498,9 +547,9 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         if (aborted(&abort_flag)) break;
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
-      if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
         const int n_kb = G.k_pad / kBK;
-        const uint32_t idesc = idesc_bf16(kBM, GROUPED ? G.bn : BN);
+        const uint32_t idesc = idesc_f16kind(kBM, GROUPED ? G.bn : BN, F16);
         const int buf = tc & 1;
         if (!ptx::mbar_wait(&acc_empty[buf], ((tc >> 1) & 1) ^ 1, &abort_flag)) {
           give_up();
@@ -562,6 +611,59 @@ __global__ void split_r_kernel(const float* __restrict__ R, int n_rec, int ld, i
   rlo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
+// R -> FP16 hi + lo of r_j R_j (one block per padded row): r_j is the power of
+// two that brings the row's largest element to [2^13, 2^14); rinv = 1 / r_j.
+__global__ void split_r16_kernel(const float* __restrict__ R, int n_rec, int ld, int k_pad, __half* __restrict__ rhi,
+                                 __half* __restrict__ rlo, float* __restrict__ rinv) {
+  __shared__ float red[32];
+  const int j = blockIdx.x;
+  const float* row = R + (size_t)j * ld;
+  float m = 0.f;
+  if (j < n_rec)
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) m = fmaxf(m, fabsf(row[k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  const float r = pow2_scale(red[0]);
+  if (j < n_rec && threadIdx.x == 0) rinv[j] = 1.f / r;
+  for (int k = threadIdx.x; k < k_pad; k += blockDim.x) {
+    const float x = (j < n_rec && k < ld) ? row[k] * r : 0.f;
+    const __half h = __float2half_rn(x);
+    rhi[(size_t)j * k_pad + k] = h;
+    rlo[(size_t)j * k_pad + k] = __float2half_rn(x - __half2float(h));
+  }
+}
+
+// Per-point FP16 scales s_p from the bound sum_b |c_b - c_b,ref| max_i |shat_b,i|
+// of the weighted-spectrum deviations (FP32 products and sums without
+// contraction, so every caller gets the same power of two).
+__device__ __forceinline__ float wscale_of(const float* th, const TcGroup& G) {
+  float c[kNB];
+  coefficients(th, dfloat{G.sin2w_hi, G.sin2w_lo}, G.cref, c);
+  float bound = 0.f;
+#pragma unroll
+  for (int b = 0; b < kNB; ++b) bound = __fadd_rn(bound, __fmul_rn(fabsf(c[b]), G.wmax[b]));
+  return pow2_scale(bound);
+}
+
+__global__ void wscale_kernel(const TcGroup g0, const float* __restrict__ theta, float* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < g0.P) out[p] = wscale_of(theta + (size_t)p * 5, g0);
+}
+
+__global__ void group_wscale_kernel(const TcGroup* __restrict__ groups, const float* __restrict__ theta,
+                                    float* __restrict__ out) {
+  const TcGroup G = groups[blockIdx.y];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < G.P) out[(size_t)G.p_off + p] = wscale_of(theta + ((size_t)G.p_off + p) * 5, G);
+}
+
 __global__ void shat_k8_kernel(const float* __restrict__ shat, int k_pad, float* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= k_pad) return;
@@ -573,29 +675,34 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int BN, bool X3>
+template <int BN, bool X3, bool F16>
 cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(fold_tc_kernel<BN, X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TcShape<BN, X3>::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(fold_tc_kernel<BN, X3, false, F16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<BN, X3>::kSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fold_tc_kernel<BN, X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(fold_tc_kernel<BN, X3, true, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               TcShape<BN, X3>::kSmem);
 }
 
-template <int BN, bool X3, bool GROUPED>
+template <int BN, bool X3, bool GROUPED, bool F16>
 cudaError_t launch_kernel(const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid, cudaStream_t s) {
-  fold_tc_kernel<BN, X3, GROUPED><<<grid, kThreads, TcShape<BN, X3>::kSmem, s>>>(mh, ml, L);
+  fold_tc_kernel<BN, X3, GROUPED, F16><<<grid, kThreads, TcShape<BN, X3>::kSmem, s>>>(mh, ml, L);
   return cudaGetLastError();
 }
 
+template <int BN, bool GROUPED>
+cudaError_t launch_prec(int precision, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid,
+                        cudaStream_t s) {
+  if (precision == SRW_FP16X3) return launch_kernel<BN, true, GROUPED, true>(mh, ml, L, grid, s);
+  if (precision == SRW_BF16X3) return launch_kernel<BN, true, GROUPED, false>(mh, ml, L, grid, s);
+  return launch_kernel<BN, false, GROUPED, false>(mh, ml, L, grid, s);
+}
+
 template <bool GROUPED>
-cudaError_t launch_any(int bn_max, bool x3, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid,
-                       cudaStream_t s) {
-  if (bn_max == 256)
-    return x3 ? launch_kernel<256, true, GROUPED>(mh, ml, L, grid, s)
-              : launch_kernel<256, false, GROUPED>(mh, ml, L, grid, s);
-  return x3 ? launch_kernel<128, true, GROUPED>(mh, ml, L, grid, s)
-            : launch_kernel<128, false, GROUPED>(mh, ml, L, grid, s);
+cudaError_t launch_any(int bn_max, int precision, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L,
+                       int grid, cudaStream_t s) {
+  if (bn_max == 256) return launch_prec<256, GROUPED>(precision, mh, ml, L, grid, s);
+  return launch_prec<128, GROUPED>(precision, mh, ml, L, grid, s);
 }
 
 EncodeTiledFn encode_fn() {
@@ -625,11 +732,12 @@ cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s) {
   const size_t n = (size_t)h->rec_pad * h->k_pad;
   split_r_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->d_R, h->n_rec, h->ld_r, h->rec_pad, h->k_pad,
                                                              h->d_rhi, h->d_rlo);
+  split_r16_kernel<<<h->rec_pad, 256, 0, s>>>(h->d_R, h->n_rec, h->ld_r, h->k_pad, h->d_rhi16, h->d_rlo16, h->d_rinv);
   shat_k8_kernel<<<(h->k_pad + 255) / 256, 256, 0, s>>>(h->d_shat, h->k_pad, h->d_shat_k8);
   return cudaGetLastError();
 }
 
-cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMap* lo) {
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo) {
   EncodeTiledFn encode = encode_fn();
   if (encode == nullptr) return cudaErrorNotSupported;
   const cuuint64_t dims[2] = {(cuuint64_t)h->k_pad, (cuuint64_t)h->rec_pad};
@@ -637,8 +745,9 @@ cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMa
   const cuuint32_t estr[2] = {1, 1};
   const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)bn};
   for (int l = 0; l < 2; ++l) {
-    CUresult r = encode(l ? lo : hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l ? (void*)h->d_rlo : (void*)h->d_rhi, dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    void* base = f16 ? (l ? (void*)h->d_rlo16 : (void*)h->d_rhi16) : (l ? (void*)h->d_rlo : (void*)h->d_rhi);
+    CUresult r = encode(l ? lo : hi, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
@@ -646,15 +755,18 @@ cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMa
 }
 
 cudaError_t tc_prepare(srw_ctx* h) {
-  cudaError_t ea = set_attr<256, true>();
-  if (ea == cudaSuccess) ea = set_attr<256, false>();
-  if (ea == cudaSuccess) ea = set_attr<128, true>();
-  if (ea == cudaSuccess) ea = set_attr<128, false>();
+  cudaError_t ea = set_attr<256, true, false>();
+  if (ea == cudaSuccess) ea = set_attr<256, false, false>();
+  if (ea == cudaSuccess) ea = set_attr<256, true, true>();
+  if (ea == cudaSuccess) ea = set_attr<128, true, false>();
+  if (ea == cudaSuccess) ea = set_attr<128, false, false>();
+  if (ea == cudaSuccess) ea = set_attr<128, true, true>();
   if (ea != cudaSuccess) return ea;
   TcMaps* maps = new (std::nothrow) TcMaps();
   if (!maps) return cudaErrorMemoryAllocation;
   for (int bi = 0; bi < 2; ++bi) {
-    const cudaError_t e = tc_encode_maps(h, bi ? 256 : 128, &maps->hi[bi], &maps->lo[bi]);
+    cudaError_t e = tc_encode_maps(h, bi ? 256 : 128, false, &maps->hi[bi], &maps->lo[bi]);
+    if (e == cudaSuccess) e = tc_encode_maps(h, bi ? 256 : 128, true, &maps->hi16[bi], &maps->lo16[bi]);
     if (e != cudaSuccess) {
       delete maps;
       return e;
@@ -686,6 +798,8 @@ TcGroup tc_group_of(const srw_ctx* h, int bn) {
   G.sin2w_hi = s2w.hi;
   G.sin2w_lo = s2w.lo;
   G.cref = h->cref;
+  G.rinv = h->d_rinv;
+  for (int b = 0; b < kNB; ++b) G.wmax[b] = h->wmax[b];
   return G;
 }
 
@@ -694,6 +808,7 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   const TcMaps* maps = static_cast<const TcMaps*>(h->tmap);
   if (!maps) return cudaErrorNotSupported;
   const int bn = cfg.bn == 256 ? 256 : 128, bi = bn == 256 ? 1 : 0;
+  const bool f16 = precision == SRW_FP16X3;
   TcLaunch L{};
   L.g0 = tc_group_of(h, bn);
   L.g0.P = P;
@@ -701,27 +816,42 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   L.items = nullptr;
   L.n_items = ((P + kBM - 1) / kBM) * L.g0.n_tiles;
   L.theta = theta;
+  L.wscale = f16 ? h->d_wscale : nullptr;
   L.parts = parts;
   L.musig_out = musig_out;
   L.status = h->d_status;
   if (n_parts) *n_parts = L.g0.n_tiles;
+  if (f16) {
+    if (h->d_wscale == nullptr || h->wscale_cap < P) return cudaErrorInvalidValue;
+    wscale_kernel<<<(P + 255) / 256, 256, 0, s>>>(L.g0, theta, h->d_wscale);
+  }
   const int grid = L.n_items < h->sm_count ? L.n_items : h->sm_count;
-  return launch_any<false>(bn, precision == SRW_BF16X3, maps->hi[bi], maps->lo[bi], L, grid, s);
+  return launch_any<false>(bn, precision, f16 ? maps->hi16[bi] : maps->hi[bi], f16 ? maps->lo16[bi] : maps->lo[bi], L,
+                           grid, s);
 }
 
-cudaError_t launch_fold_tc_group(int bn_max, bool x3, const TcGroup* d_groups, const int4* d_items, int n_slots,
-                                 int n_cta, const float* theta, double* parts, unsigned* status, cudaStream_t s) {
+cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
+                                cudaStream_t s) {
+  if (n_groups < 1 || max_P < 1) return cudaSuccess;
+  group_wscale_kernel<<<dim3((max_P + 255) / 256, n_groups), 256, 0, s>>>(d_groups, theta, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_groups, const int4* d_items, int n_slots,
+                                 int n_cta, const float* theta, const float* wscale, double* parts, unsigned* status,
+                                 cudaStream_t s) {
   if (n_cta < 1) return cudaSuccess;
   TcLaunch L{};
   L.groups = d_groups;
   L.items = d_items;
   L.n_items = n_slots;
   L.theta = theta;
+  L.wscale = wscale;
   L.parts = parts;
   L.musig_out = nullptr;
   L.status = status;
   static const CUtensorMap unused{};  // grouped launches read each configuration's maps from its descriptor
-  return launch_any<true>(bn_max == 256 ? 256 : 128, x3, unused, unused, L, n_cta, s);
+  return launch_any<true>(bn_max == 256 ? 256 : 128, precision, unused, unused, L, n_cta, s);
 }
 
 int tc_max_groups() { return kMaxGroups; }

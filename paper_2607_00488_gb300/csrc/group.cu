@@ -79,11 +79,12 @@ struct srw_group_ctx {
   int P_total = 0, P_max = 0;
   std::vector<unsigned long long> versions;
   bool tensor_ok = true;
-  srw_group_plan plan[2];           // SRW_BF16, SRW_BF16X3
+  srw_group_plan plan[3];           // SRW_BF16, SRW_BF16X3, SRW_FP16X3
   GroupPart* d_simt_gparts = nullptr;  // SRW_FP32
   size_t simt_parts = 0;
   double* d_parts = nullptr;
   size_t parts_cap = 0;
+  float* d_wscale = nullptr;        // per-point FP16 scales (SRW_FP16X3)
   float* d_theta = nullptr;         // staging for host calls
   double* d_out = nullptr;
   unsigned* d_status = nullptr;
@@ -197,7 +198,7 @@ srw_status build_plan(srw_group g, int pi, int cand) {
     desc[i] = G;
     gparts[i] = GroupPart{parts_off, G.n_tiles, G.P, G.p_off, 0, h->d_cdata};
     parts_off += (long long)G.n_tiles * G.P;
-    const cudaError_t e = srw::tc_encode_maps(h, bn, &maps[2 * (size_t)i], &maps[2 * (size_t)i + 1]);
+    const cudaError_t e = srw::tc_encode_maps(h, bn, pi + 1 == SRW_FP16X3, &maps[2 * (size_t)i], &maps[2 * (size_t)i + 1]);
     if (e != cudaSuccess) return gcuda(g, e, "tensor maps");
     const double cost = item_cost(h->k_pad / kBK, bn);
     const int m_tiles = (G.P + kBM - 1) / kBM;
@@ -297,9 +298,11 @@ srw_status run(srw_group g, const float* th, double* o, int precision, cudaStrea
   }
   srw_status st = ensure_parts(g, pl.n_parts);
   if (st != SRW_OK) return st;
+  if (precision == SRW_FP16X3)
+    G_CUDA(g, srw::launch_group_wscale(pl.d_groups, g->n, g->P_max, th, g->d_wscale, s), "FP16 scales");
   if (g->profile) G_CUDA(g, cudaEventRecord(g->ev[0], s), "event");
-  G_CUDA(g, srw::launch_fold_tc_group(pl.bn_max, precision == SRW_BF16X3, pl.d_groups, pl.d_items, pl.n_slots,
-                                      pl.n_cta, th, g->d_parts, g->d_status, s),
+  G_CUDA(g, srw::launch_fold_tc_group(pl.bn_max, precision, pl.d_groups, pl.d_items, pl.n_slots, pl.n_cta, th,
+                                      precision == SRW_FP16X3 ? g->d_wscale : nullptr, g->d_parts, g->d_status, s),
          "grouped fold");
   if (g->profile) G_CUDA(g, cudaEventRecord(g->ev[1], s), "event");
   G_CUDA(g, srw::launch_group_reduce(pl.d_gparts, g->n, g->P_max, g->d_parts, o, g->d_status, s), "reduce");
@@ -307,7 +310,7 @@ srw_status run(srw_group g, const float* th, double* o, int precision, cudaStrea
 }
 
 srw_status check_precision(srw_group g, int precision) {
-  if (precision < SRW_FP32 || precision > SRW_BF16X3) return gfail(g, SRW_EINVAL, "bad precision");
+  if (precision < SRW_FP32 || precision > SRW_FP16X3) return gfail(g, SRW_EINVAL, "bad precision");
   if (precision != SRW_FP32 && !g->tensor_ok)
     return gfail(g, SRW_EUNSUPPORTED, "tensor-core fold unavailable on this device");
   return SRW_OK;
@@ -353,6 +356,7 @@ srw_status srw_group_create(const srw_handle* handles, int n, const int* P, srw_
   if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_theta, sizeof(float) * 5 * total);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_wscale, sizeof(float) * total);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_out, sizeof(double) * total);
   if (e != cudaSuccess) {
     srw_group_destroy(g);
@@ -440,7 +444,7 @@ srw_status srw_group_autotune(srw_group g, srw_precision precision, void* stream
 
 srw_status srw_group_set_schedule(srw_group g, srw_precision precision, int candidate) {
   if (!g) return SRW_EINVAL;
-  if (precision != SRW_BF16 && precision != SRW_BF16X3)
+  if (precision != SRW_BF16 && precision != SRW_BF16X3 && precision != SRW_FP16X3)
     return gfail(g, SRW_EINVAL, "schedules exist for the tensor-core precisions only");
   if (candidate < 0 || candidate > 2) return gfail(g, SRW_EINVAL, "candidate must be 0, 1 or 2");
   refresh_if_changed(g);
@@ -450,7 +454,7 @@ srw_status srw_group_set_schedule(srw_group g, srw_precision precision, int cand
 srw_status srw_group_schedule(srw_group g, srw_precision precision, int* bn_max, int* bn, int* n_items, int* n_cta,
                               int* candidate) {
   if (!g) return SRW_EINVAL;
-  if (precision != SRW_BF16 && precision != SRW_BF16X3)
+  if (precision != SRW_BF16 && precision != SRW_BF16X3 && precision != SRW_FP16X3)
     return gfail(g, SRW_EINVAL, "schedules exist for the tensor-core precisions only");
   refresh_if_changed(g);
   srw_group_plan& pl = g->plan[(int)precision - 1];
@@ -494,6 +498,7 @@ srw_status srw_group_destroy(srw_group g) {
   invalidate(g);
   gfree(g->d_parts);
   gfree(g->d_theta);
+  gfree(g->d_wscale);
   gfree(g->d_out);
   gfree(g->d_status);
   for (auto& ev : g->ev)

@@ -127,7 +127,7 @@ static void release(srw_ctx* h) {
   tc_release(h);
   dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_shat_lo); dfree(h->d_shat_k8); dfree(h->d_node64); dfree(h->d_bin_count); dfree(h->d_bin_f);
   dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis); dfree(h->d_ssm64); dfree(h->d_esm64);
-  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo);
+  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
   dfree(h->d_status); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
@@ -159,6 +159,17 @@ static srw_status ensure_staging(srw_ctx* h, int P) {
   SRW_CUDA(h, cudaMalloc(&h->d_theta, sizeof(float) * 5 * (size_t)cap), "staging theta");
   SRW_CUDA(h, cudaMalloc(&h->d_out, sizeof(double) * (size_t)cap), "staging out");
   h->stage_cap = cap;
+  return SRW_OK;
+}
+
+// Per-point scale buffer of the FP16 split.
+static srw_status ensure_wscale(srw_ctx* h, int P) {
+  if (P <= h->wscale_cap) return SRW_OK;
+  const int cap = std::max(P, 2 * h->wscale_cap);
+  destroy_graphs(h);
+  dfree(h->d_wscale);
+  SRW_CUDA(h, cudaMalloc(&h->d_wscale, sizeof(float) * (size_t)cap), "FP16 scales");
+  h->wscale_cap = cap;
   return SRW_OK;
 }
 
@@ -489,13 +500,25 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
     CREATE_CUDA(dalloc(h, &h->d_rhi, (size_t)h->rec_pad * h->k_pad), "alloc R hi");
     CREATE_CUDA(dalloc(h, &h->d_rlo, (size_t)h->rec_pad * h->k_pad), "alloc R lo");
     CREATE_CUDA(dalloc(h, &h->d_shat_k8, (size_t)kNB * h->k_pad), "alloc shat k-major");
+    CREATE_CUDA(dalloc(h, &h->d_rhi16, (size_t)h->rec_pad * h->k_pad), "alloc R hi (FP16)");
+    CREATE_CUDA(dalloc(h, &h->d_rlo16, (size_t)h->rec_pad * h->k_pad), "alloc R lo (FP16)");
+    CREATE_CUDA(dalloc(h, &h->d_rinv, (size_t)h->n_rec), "alloc R row scales");
+    {  // bound of the coefficient spectra for the FP16 scales of the weighted spectra
+      std::vector<float> sh((size_t)kNB * h->k_pad);
+      CREATE_CUDA(cudaMemcpy(sh.data(), h->d_shat, sizeof(float) * sh.size(), cudaMemcpyDeviceToHost), "read shat");
+      for (int b = 0; b < kNB; ++b) {
+        float m = 0.f;
+        for (int k = 0; k < h->k_pad; ++k) m = std::max(m, std::fabs(sh[(size_t)b * h->k_pad + k]));
+        h->wmax[b] = m;
+      }
+    }
     CREATE_CUDA(launch_split_r(h, s), "split R");
     CREATE_CUDA(cudaStreamSynchronize(s), "split sync");
     CREATE_CUDA(tc_prepare(h), "tensor map encode");
     h->tensor_ok = true;
   }
   h->cfg[0] = FoldConfig{0, 128, 1, 0};
-  h->cfg[1] = h->cfg[2] = tc_num_configs() > 0 ? tc_config(0) : FoldConfig{0, 128, 1, 0};
+  h->cfg[1] = h->cfg[2] = h->cfg[3] = tc_num_configs() > 0 ? tc_config(0) : FoldConfig{0, 128, 1, 0};
   *out = h;
   return SRW_OK;
 #undef CREATE_CUDA
@@ -578,7 +601,7 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
   if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
   if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
-  if (precision < SRW_FP32 || precision > SRW_BF16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (precision < SRW_FP32 || precision > SRW_FP16X3) return fail(h, SRW_EINVAL, "bad precision");
   if (!h->has_data) return fail(h, SRW_ENODATA, "call srw_set_data first");
   if (where != SRW_HOST && where != SRW_DEVICE) return fail(h, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
   if (precision != SRW_FP32 && !h->tensor_ok)
@@ -620,6 +643,7 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   } else {
     const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
     st = ensure_bparts(h, (size_t)n_parts_max * P);
+    if (st == SRW_OK && precision == SRW_FP16X3) st = ensure_wscale(h, P);
     if (st != SRW_OK) return st;
     const FoldConfig cfg = h->cfg[precision];
     st = run_graph(h, 2, precision, P, th, o, s, [&](cudaStream_t cs) {
@@ -660,13 +684,17 @@ srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* ou
   if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
   if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
   if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
-  if (precision < SRW_FP32 || precision > SRW_BF16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (precision < SRW_FP32 || precision > SRW_FP16X3) return fail(h, SRW_EINVAL, "bad precision");
   if (precision != SRW_FP32 && !h->tensor_ok)
     return fail(h, SRW_EUNSUPPORTED, "tensor-core fold unavailable on this device");
   cudaStream_t s = pick_stream(h, stream);
   const float* th = theta;
   float* o = out;
   float* d_tmp = nullptr;
+  if (precision == SRW_FP16X3) {
+    srw_status st = ensure_wscale(h, P);
+    if (st != SRW_OK) return st;
+  }
   if (where == SRW_HOST) {
     for (size_t q = 0; q < (size_t)P * 5; ++q)
       if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
@@ -756,6 +784,7 @@ srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char
   if (st != SRW_OK) return st;
   const int n_parts_max = h->rec_pad / 128;
   st = ensure_bparts(h, (size_t)n_parts_max * P);
+  if (st == SRW_OK && pr == SRW_FP16X3) st = ensure_wscale(h, P);
   if (st != SRW_OK) return st;
   // deterministic in-box points for timing
   std::vector<float> th((size_t)P * 5);

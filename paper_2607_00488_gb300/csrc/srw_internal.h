@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -89,6 +90,8 @@ struct TcGroup {
   int bn, n_tiles;             // rec tile width (128 or 256) and number of rec tiles
   float sin2w_hi, sin2w_lo;
   CoefRef cref;
+  const float* rinv;           // SRW_FP16X3: [n_rec] inverse power-of-two row scales of R
+  float wmax[kNB];             // SRW_FP16X3: max_i |shat_b,i| (bound of the weighted-spectrum deviations)
 };
 
 // Where the per-tile partial sums of one configuration live, for the final
@@ -142,6 +145,12 @@ struct srw_ctx {
   float* d_R = nullptr;        // [n_rec][ld_r]
   __nv_bfloat16* d_rhi = nullptr;  // [rec_pad][k_pad]
   __nv_bfloat16* d_rlo = nullptr;
+  __half* d_rhi16 = nullptr;       // [rec_pad][k_pad] FP16 split of R scaled by row (SRW_FP16X3)
+  __half* d_rlo16 = nullptr;
+  float* d_rinv = nullptr;         // [n_rec] inverse row scales of the FP16 split
+  float wmax[8] = {};              // max_i |shat_b,i|
+  float* d_wscale = nullptr;       // [P] per-point scales of the FP16 split (batched scratch)
+  int wscale_cap = 0;
 
   // data
   double* d_n64 = nullptr;
@@ -169,8 +178,8 @@ struct srw_ctx {
 
   cudaStream_t own_stream = nullptr;
   std::vector<srw::GraphEntry> graphs;
-  srw::FoldConfig cfg[3];      // per precision
-  int cfg_index[3] = {-1, -1, -1};
+  srw::FoldConfig cfg[4];      // per precision
+  int cfg_index[4] = {-1, -1, -1, -1};
   bool tensor_ok = false;
   void* tmap = nullptr;        // TMA descriptors for R hi/lo (tcgen05 path)
   int profile = 0;             // record events around the fold launch
@@ -225,17 +234,22 @@ FoldConfig tc_config(int i);
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
                            double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr);
 cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s);
+// Per-point power-of-two scales of the FP16 split for a grouped launch.
+cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
+                                cudaStream_t s);
 int tc_max_groups();
 // Descriptor of handle h as a configuration with rec tile bn (maps left null).
 TcGroup tc_group_of(const srw_ctx* h, int bn);
-// Tensor maps of h's BF16 hi / lo response with a box of 64 K x bn rows.
-cudaError_t tc_encode_maps(const srw_ctx* h, int bn, CUtensorMap* hi, CUtensorMap* lo);
+// Tensor maps of h's hi / lo response (FP16 split if f16, else BF16) with a
+// box of 64 K x bn rows.
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo);
 // One persistent launch of n_cta CTAs over several configurations.  Slot
 // k * n_cta + b of items (n_slots in all) is CTA b's k-th item {group, m0,
 // n0, 0}; a group < 0 ends that CTA's list.  bn_max (128 or 256) bounds every
 // group's bn.
-cudaError_t launch_fold_tc_group(int bn_max, bool x3, const TcGroup* d_groups, const int4* d_items, int n_slots,
-                                 int n_cta, const float* theta, double* parts, unsigned* status, cudaStream_t s);
+cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_groups, const int4* d_items, int n_slots,
+                                 int n_cta, const float* theta, const float* wscale, double* parts, unsigned* status,
+                                 cudaStream_t s);
 // -2 ln L of every point of a grouped call from its per-tile partial sums.
 cudaError_t launch_group_reduce(const GroupPart* d_gparts, int n_groups, int max_P, const double* parts,
                                 double* out, unsigned* status, cudaStream_t s);

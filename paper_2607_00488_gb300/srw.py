@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libsrw.so")
 
 SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOUT, SRW_EUNSUPPORTED = range(8)
 SRW_HOST, SRW_DEVICE = 0, 1
-SRW_FP32, SRW_BF16, SRW_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3}
+SRW_FP32, SRW_BF16, SRW_BF16X3, SRW_FP16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3, "fp16x3": SRW_FP16X3}
 
 # Entry points declared in include/srw.h (checked by the test-suite).
 EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "srw_loglik", "srw_loglik_points", "srw_get_basis",

@@ -48,7 +48,7 @@ def _asimov(wl, **kw):
     return workloads.poisson_counts(m.mu(np.zeros(5)), 3)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
 def test_ragged_sizes_and_single_point(srw, prec):
     wl = small_workload()
     counts = _asimov(wl)
@@ -72,7 +72,7 @@ def test_mask_and_empty_bins(srw):
     ref = _oracle(wl, counts, mask)
     th = np.concatenate([np.zeros((1, 5), np.float32), workloads.theta_box(7, 3, eps_max=0.02, mu_max=0.5)])
     with srw.Likelihood(wl, counts, mask=mask) as lk:
-        for prec, tol in (("fp32", 1e-4), ("bf16x3", 1e-3)):
+        for prec, tol in (("fp32", 1e-4), ("bf16x3", 1e-3), ("fp16x3", 1e-3)):
             got = lk.loglik(th, srw.PRECISIONS[prec])
             np.testing.assert_allclose(got, ref.neg2lnl_batch(th.astype(np.float64)), rtol=0, atol=tol)
         single = lk.loglik(th[2:3], srw.SRW_FP32)
@@ -116,7 +116,7 @@ def test_domain_error_gives_inf(srw):
     counts[7] = 3.0                        # ...but it holds events
     th = np.zeros((2, 5), np.float32)
     with srw.Likelihood(wl, counts) as lk:
-        for prec in ("fp32", "bf16x3"):
+        for prec in ("fp32", "bf16x3", "fp16x3"):
             assert np.all(np.isinf(lk.loglik(th, srw.PRECISIONS[prec])))
         assert np.isinf(lk.loglik(th[:1], srw.SRW_FP32)[0])
     assert O.neg2lnl(O.OracleModel.from_workload(wl).mu_sig(np.zeros(5)) + wl["bkg"].sum(0), counts) == np.inf

@@ -33,7 +33,7 @@ import workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-4, 2: 1e-3}  # SRW_FP32, SRW_BF16X3 in the fit region
+TOL = {0: 1e-4, 2: 1e-3, 3: 1e-3}  # SRW_FP32, SRW_BF16X3, SRW_FP16X3 in the fit region
 
 
 @pytest.fixture(scope="module")
@@ -115,7 +115,7 @@ def _split(values, members):
     return out
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_group_equals_member_folds_bitwise(srw, small, prec):
     members, grp = small
     grp.set_schedule(prec, 0)  # every configuration with 256-bin tiles, as the members' default
@@ -181,14 +181,16 @@ def _check_vs_oracle(srw, members, got_by_member, prec, idx_fn):
     return worst
 
 
-@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("prec", [0, 2, 3])
 def test_group_vs_oracle(srw, small, prec):
     members, grp = small
-    grp.set_schedule(2, 1)
+    if prec:
+        grp.set_schedule(prec, 1)
     got = _split(grp.loglik(_theta_all(members), prec), members)
     worst = _check_vs_oracle(srw, members, got, prec, lambda m: sorted({0, min(1, m.P - 1), m.P - 1}))
     worst.sort(reverse=True)
     print("largest |d| (d, budget, fit, exposure, config, point):", worst[:3])
+    print("fit region |d| by exposure:", sorted((round(w[3]), w[0]) for w in worst if w[2]))
 
 
 def test_group_picks_up_reference_and_data_changes(srw, small):
