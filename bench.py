@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-grouped", action="store_true", help="skip the 64-configuration grouped measurement")
     ap.add_argument("--grouped-only", action="store_true",
                     help="only the grouped measurement (for profiling its launch)")
+    ap.add_argument("--groups", type=int, default=64, help="configurations of the grouped workload")
+    ap.add_argument("--group-scale", type=float, default=1.0,
+                    help="size factor of the grouped workload (profiling captures of a smaller case)")
     return ap.parse_args()
 
 
@@ -226,8 +229,11 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
     import numpy as np
     import torch
 
-    gw = workloads.uneven_groups_workload()
-    counts = workloads.load_group_counts(gw)
+    gw = workloads.uneven_groups_workload(n_groups=args.groups, scale=args.group_scale)
+    if args.groups == 64 and args.group_scale == 1.0:
+        counts = workloads.load_group_counts(gw)
+    else:  # smaller profiling cases: flat pseudo-data (the fold does the same work for any counts)
+        counts = [workloads.poisson_counts(np.full(s["n_rec"], s["exposure"] / s["n_rec"]), 0) for s in gw["groups"]]
     members, thetas, useful = [], [], 0.0
     for g, spec in enumerate(gw["groups"]):
         wl = workloads.uneven_group_inputs(gw, g)
