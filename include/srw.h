@@ -294,6 +294,40 @@ srw_status srw_group_profile_read(srw_group g, float* fold_ms);
 const char* srw_group_last_error(srw_group g);
 srw_status srw_group_destroy(srw_group g);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate (the paper has no counterpart; it serves dense scans):
+ * a GELU MLP theta -> log mu_j (expected counts per reconstructed bin of
+ * handle h), widths 5 -> 256 -> 256 -> 256 -> n_rec, trained on spectra of
+ * the exact path and used to pre-screen scans, with the exact path as judge.
+ *   x = (theta - centre) / half_width;  h_k = gelu(W_k h_{k-1} + b_k)  (k = 1..3,
+ *   gelu(z) = z Phi(z));  y = W_4 h_3 + b_4;  log mu_j = m_j + s_j y_j
+ * with per-bin standardization (m_j, s_j) of the training targets (identity
+ * until srw_surrogate_fit sets it).  All products run on the tcgen05 tensor
+ * cores in BF16 with FP32 accumulation; Adam keeps FP32 master weights.
+ * Weight arrays (host, FP32, row-major) are passed as 8 pointers
+ * {W1 [256][5], b1 [256], W2 [256][256], b2, W3 [256][256], b3, W4 [n_rec][256], b4 [n_rec]}.
+ * The handle must have data set and the tensor-core path; it must outlive s.
+ */
+typedef struct srw_surrogate_ctx* srw_surrogate;
+
+srw_status srw_surrogate_create(srw_handle h, const float* centre, const float* half_width,
+                                const float* const* weights, srw_surrogate* out);
+/* Replace the weights (resets the Adam state) / read the FP32 master weights. */
+srw_status srw_surrogate_set_weights(srw_surrogate s, const float* const* weights);
+srw_status srw_surrogate_get_weights(srw_surrogate s, float* const* weights);
+/* Network output y (before de-standardization) for P points: y [P][n_rec] (host). */
+srw_status srw_surrogate_forward(srw_surrogate s, const float* theta, int P, float* y);
+/* Mean squared error of y against targets [P][n_rec] (host) and its gradients
+ * (8 host arrays shaped like the weights); no update. */
+srw_status srw_surrogate_gradients(srw_surrogate s, const float* theta, const float* targets, int P,
+                                   float* const* grads, double* loss);
+/* One training step (forward, backward, Adam with beta1 0.9, beta2 0.999,
+ * eps 1e-8, learning rate lr) on P points; loss = the step's mean squared error. */
+srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const float* targets, int P, float lr,
+                                    double* loss);
+const char* srw_surrogate_last_error(srw_surrogate s);
+srw_status srw_surrogate_destroy(srw_surrogate s);
+
 const char* srw_last_error(srw_handle h);
 const char* srw_status_string(srw_status s);
 srw_status srw_destroy(srw_handle h);

@@ -19,6 +19,7 @@ from .srw import (  # noqa: F401
     GroupedLikelihood,
     Likelihood,
     SrwError,
+    Surrogate,
     lib,
     srw_autotune,
     srw_create,

@@ -27,7 +27,9 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_autotune", "srw_info", "srw_set_reference", "srw_profile", "srw_profile_read", "srw_last_error", "srw_status_string",
            "srw_destroy", "srw_loglik_point_noalloc", "srw_noalloc_last_error", "srw_group_create", "srw_group_loglik",
            "srw_group_autotune", "srw_group_set_schedule", "srw_group_schedule", "srw_group_profile", "srw_group_profile_read",
-           "srw_group_last_error", "srw_group_destroy")
+           "srw_group_last_error", "srw_group_destroy", "srw_surrogate_create", "srw_surrogate_set_weights",
+           "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
+           "srw_surrogate_last_error", "srw_surrogate_destroy")
 
 
 class SrwError(RuntimeError):
@@ -100,8 +102,18 @@ def lib():
         L.srw_group_last_error.argtypes = [vp]
         L.srw_group_last_error.restype = ctypes.c_char_p
         L.srw_group_destroy.argtypes = [vp]
+        L.srw_surrogate_create.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.srw_surrogate_set_weights.argtypes = [vp, vp]
+        L.srw_surrogate_get_weights.argtypes = [vp, vp]
+        L.srw_surrogate_forward.argtypes = [vp, vp, ip, vp]
+        L.srw_surrogate_gradients.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
+        L.srw_surrogate_train_step.argtypes = [vp, vp, vp, ip, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+        L.srw_surrogate_last_error.argtypes = [vp]
+        L.srw_surrogate_last_error.restype = ctypes.c_char_p
+        L.srw_surrogate_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name not in ("srw_last_error", "srw_status_string", "srw_noalloc_last_error", "srw_group_last_error"):
+            if name not in ("srw_last_error", "srw_status_string", "srw_noalloc_last_error", "srw_group_last_error",
+                            "srw_surrogate_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -358,6 +370,80 @@ def srw_group_destroy(g):
         lib().srw_group_destroy(g)
 
 
+def _scheck(status, sg):
+    if status != SRW_OK:
+        msg = (lib().srw_surrogate_last_error(sg) if sg else lib().srw_status_string(status)).decode(errors="replace")
+        raise SrwError(status, msg)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr_array(arrays):
+    """ctypes array of 8 pointers to float32 host arrays (kept alive by the caller)."""
+    return (ctypes.c_void_p * len(arrays))(*[a.ctypes.data for a in arrays])
+
+
+def srw_surrogate_create(h, centre, half_width, params):
+    """params: [(W, b), ...] of the four layers (float32 host arrays)."""
+    flat = [_f32(x) for W, b in params for x in (W, b)]
+    c, hw = _f32(centre), _f32(half_width)
+    out = ctypes.c_void_p()
+    _scheck(lib().srw_surrogate_create(h, c.ctypes.data, hw.ctypes.data, _ptr_array(flat), ctypes.byref(out)), None)
+    return out
+
+
+def srw_surrogate_set_weights(sg, params):
+    flat = [_f32(x) for W, b in params for x in (W, b)]
+    _scheck(lib().srw_surrogate_set_weights(sg, _ptr_array(flat)), sg)
+
+
+def _like(params):
+    return [np.empty_like(_f32(x)) for W, b in params for x in (W, b)]
+
+
+def _pairs(flat):
+    return [(flat[2 * k], flat[2 * k + 1]) for k in range(len(flat) // 2)]
+
+
+def srw_surrogate_get_weights(sg, shapes_like):
+    flat = _like(shapes_like)
+    _scheck(lib().srw_surrogate_get_weights(sg, _ptr_array(flat)), sg)
+    return _pairs(flat)
+
+
+def srw_surrogate_forward(sg, theta, n_out):
+    th = _f32(theta).reshape(-1, 5)
+    y = np.empty((th.shape[0], n_out), dtype=np.float32)
+    _scheck(lib().srw_surrogate_forward(sg, th.ctypes.data, th.shape[0], y.ctypes.data), sg)
+    return y
+
+
+def srw_surrogate_gradients(sg, theta, targets, shapes_like):
+    th = _f32(theta).reshape(-1, 5)
+    t = _f32(targets)
+    flat = _like(shapes_like)
+    loss = ctypes.c_double()
+    _scheck(lib().srw_surrogate_gradients(sg, th.ctypes.data, t.ctypes.data, th.shape[0], _ptr_array(flat),
+                                          ctypes.byref(loss)), sg)
+    return loss.value, _pairs(flat)
+
+
+def srw_surrogate_train_step(sg, theta, targets, lr):
+    th = _f32(theta).reshape(-1, 5)
+    t = _f32(targets)
+    loss = ctypes.c_double()
+    _scheck(lib().srw_surrogate_train_step(sg, th.ctypes.data, t.ctypes.data, th.shape[0], ctypes.c_float(lr),
+                                           ctypes.byref(loss)), sg)
+    return loss.value
+
+
+def srw_surrogate_destroy(sg):
+    if sg:
+        lib().srw_surrogate_destroy(sg)
+
+
 def srw_last_error(h):
     return lib().srw_last_error(h).decode(errors="replace")
 
@@ -451,6 +537,48 @@ class GroupedLikelihood:
     def close(self):
         if self.handle:
             srw_group_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """The learned surrogate of one likelihood context (``Likelihood``)."""
+
+    def __init__(self, likelihood, params, centre, half_width):
+        self.lk = likelihood  # the surrogate does not own the handle; keep it alive
+        self.shapes = [(np.zeros_like(_f32(W)), np.zeros_like(_f32(b))) for W, b in params]
+        self.n_out = self.shapes[-1][1].size
+        self.handle = srw_surrogate_create(likelihood.handle, centre, half_width, params)
+
+    def set_weights(self, params):
+        srw_surrogate_set_weights(self.handle, params)
+
+    def weights(self):
+        return srw_surrogate_get_weights(self.handle, self.shapes)
+
+    def forward(self, theta):
+        return srw_surrogate_forward(self.handle, theta, self.n_out)
+
+    def gradients(self, theta, targets):
+        return srw_surrogate_gradients(self.handle, theta, targets, self.shapes)
+
+    def train_step(self, theta, targets, lr):
+        return srw_surrogate_train_step(self.handle, theta, targets, lr)
+
+    def close(self):
+        if self.handle:
+            srw_surrogate_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):
