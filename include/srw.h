@@ -325,6 +325,83 @@ srw_status srw_surrogate_gradients(srw_surrogate s, const float* theta, const fl
  * eps 1e-8, learning rate lr) on P points; loss = the step's mean squared error. */
 srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const float* targets, int P, float lr,
                                     double* loss);
+/* Train on n points (host theta [n][5], e.g. uniform in the box): the exact
+ * path computes the expected counts mu = R W(theta) + b (srw_spectrum_batch in
+ * `precision`, plus the summed background), the targets are log mu
+ * standardized per bin over the training set (which also sets m_j, s_j), and
+ * `epochs` passes of Adam over batches of `batch` points (fixed order) run with
+ * a cosine learning-rate decay from lr to lr_final.  epoch_loss (may be NULL)
+ * receives the mean squared error of each epoch.  Needs n * ceil(n_rec/256) *
+ * 1 KB of device memory for the targets (8.4 GB at n = 1e6, n_rec = 2048). */
+typedef struct {
+  int batch;           /* points per step: a positive multiple of 128 */
+  int epochs;
+  float lr, lr_final;
+  int precision;       /* srw_precision of the exact spectra */
+} srw_fit_opts;
+srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* opts,
+                             float* epoch_loss);
+
+/* Surrogate -2 ln L (eq. logL with mu_j = exp(m_j + s_j y_j), the handle's data
+ * and mask) for P points; `where` and `stream` as in srw_loglik. */
+srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, double* out, int where, void* stream);
+
+/* Pre-screened scan over the Sobol points with sequence indices [first,
+ * first + n_points) mapped to the box (Sobol 1967 with Joe & Kuo 2008
+ * direction numbers, Gray-code order; point 0 is the box corner):
+ *   1. held-out check: the exact path and the surrogate on the n_check points
+ *      check_theta; the box is cut into cells_per_dim^5 cells; a cell is
+ *      flagged when its largest |d(-2lnL)| exceeds tol or it holds no check
+ *      point;
+ *   2. the surrogate's -2 ln L of every scan point;
+ *   3. exact re-evaluation (in `precision`) of the points whose surrogate value
+ *      is among the lowest keep_frac, plus
+ *        SRW_SCAN_FLAG_CELLS : every point of every flagged cell;
+ *        SRW_SCAN_ERROR_BARS : afterwards, every other point whose surrogate
+ *          value minus margin_factor x max(its cell's held-out |d|, tol) is at
+ *          or below the best exact value found (a point that could still be
+ *          the minimum within the cell's error bar; cells without a check
+ *          point: all of their points);
+ *   4. the exact minimum among the re-evaluated points.
+ * With n_check = 0 no cell is flagged (SRW_SCAN_FLAG_CELLS) or every cell
+ * counts as unchecked (SRW_SCAN_ERROR_BARS). */
+typedef enum { SRW_SCAN_FLAG_CELLS = 0, SRW_SCAN_ERROR_BARS = 1 } srw_scan_rule;
+typedef struct {
+  long long first, n_points;
+  double keep_frac;
+  const float* check_theta;
+  int n_check;
+  double tol;
+  int cells_per_dim;           /* 1..16 */
+  int precision;
+  int rule;                    /* srw_scan_rule */
+  double margin_factor;        /* >= 1 (SRW_SCAN_ERROR_BARS) */
+} srw_scan_opts;
+typedef struct {
+  double best_value;             /* exact -2 ln L minimum among the re-evaluated points */
+  long long best_index;          /* its Sobol index */
+  float best_theta[5];
+  double surrogate_min;          /* smallest surrogate value of the scan */
+  long long n_kept;              /* points with surrogate values at or below the keep_frac threshold */
+  long long n_selected;          /* all re-evaluated points */
+  long long n_rescued;           /* of which added by the error-bar pass (SRW_SCAN_ERROR_BARS) */
+  int n_cells, n_flagged_cells;
+  double check_max_abs_d;        /* largest |d(-2lnL)| on the check set */
+  float ms_check, ms_surrogate, ms_select, ms_exact;  /* device time of each phase */
+} srw_scan_result;
+srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* opts, srw_scan_result* res);
+
+/* The same scan without the surrogate: the exact path on every point; the
+ * minimum, its index and the device time. */
+srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long n_points, int precision,
+                                    double* best_value, long long* best_index, float* ms);
+
+/* Points first .. first + count - 1 of the scan's Sobol sequence, mapped to the
+ * box (host theta [count][5]). */
+srw_status srw_surrogate_sobol(srw_surrogate s, long long first, int count, float* theta);
+/* The per-bin standardization m_j, s_j of log mu (n_rec floats each, host). */
+srw_status srw_surrogate_get_standardization(srw_surrogate s, float* mean, float* stdv);
+
 const char* srw_surrogate_last_error(srw_surrogate s);
 srw_status srw_surrogate_destroy(srw_surrogate s);
 

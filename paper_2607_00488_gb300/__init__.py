@@ -16,6 +16,8 @@ from .srw import (  # noqa: F401
     SRW_FP16X3,
     SRW_FP32,
     SRW_HOST,
+    SRW_SCAN_ERROR_BARS,
+    SRW_SCAN_FLAG_CELLS,
     GroupedLikelihood,
     Likelihood,
     SrwError,

@@ -46,7 +46,8 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr int kTmaWarp = 0;
 constexpr int kMmaWarp = 1;
-constexpr int kGemmThreads = 6 * 32;
+constexpr int kEpiWarps = 8;                     // two per TMEM lane quarter, each on half the columns
+constexpr int kGemmThreads = (2 + kEpiWarps) * 32;
 constexpr int kIn = 5;          // theta components
 constexpr int kInPad = 128;     // padded input width (one 128-row operand tile)
 constexpr int kHidden = 256;
@@ -64,10 +65,8 @@ struct EpiArgs {
   const float* aux;      // fit: targets [M][N]; backward data: gelu'(z) [M][N]
   float scale;           // fit: 2 / (rows_valid * cols_valid)
   double* loss;          // fit: += sum of squared errors
-  const float* mean;     // scan: per-bin mean / std of log mu
-  const float* stdv;
-  const float2* nb;      // scan: {n_j, or -1 where masked, unused}
-  double* parts;         // scan: per (column tile, row) partial sums of the deviance
+  const float4* binc;    // scan: per bin {m_j + s_j b_j, s_j, n_j, n_j ln n_j - n_j} (masked: {0, 0, 0, -1})
+  double* parts;         // scan: per (column half-tile, row) partial sums of the deviance
 };
 
 template <int BN>
@@ -126,7 +125,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&acc_full[b], 1);
-      ptx::mbar_init(&acc_empty[b], 4);
+      ptx::mbar_init(&acc_empty[b], kEpiWarps);
     }
     ptx::mbar_init(&drain, 1);
     abort_flag = 0u;
@@ -206,7 +205,8 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lanes 32 q .. 32 q + 31
+    const int q = warp & 3;                  // TMEM lanes 32 q .. 32 q + 31
+    const int half = (warp - 2) >> 2;        // columns [half BN/2, (half + 1) BN/2)
     int tc = -1;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
       ++tc;
@@ -225,7 +225,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
       dfloat dev = {0.f, 0.f};
       bool infinite = false;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
         const int n = n0 + c0;
         float v[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
@@ -273,18 +273,14 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
 #pragma unroll
           for (int k = 0; k < 16; ++k) v[k] += __ldg(E.bias + n + k);
           store_f32x16(E.out_f32 + (size_t)m * N + n, v);
-        } else {  // kFwdScan: Poisson deviance of mu = exp(m + s y)
+        } else {  // kFwdScan: deviance of mu = exp(lm), lm = m + s (y + b) = log mu:
+                  // t = mu - n + n ln(n / mu) = mu - n lm + (n ln n - n)
           float ts = 0.f;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const int j = n + k;
-            float nj = -1.f, mu = 1.f;
-            if (j < E.cols_valid) {
-              nj = __ldg(&E.nb[j].x);
-              mu = expf(__ldg(E.mean + j) + __ldg(E.stdv + j) * (v[k] + __ldg(E.bias + j)));
-            }
-            const float tj = poisson_term_f32_sel(mu, nj);
-            ts += nj >= 0.f ? tj : 0.f;
+            const float4 c = __ldg(E.binc + n + k);
+            const float lm = fmaf(c.y, v[k], c.x);
+            ts += fmaf(-c.z, lm, __expf(lm) + c.w);
           }
           if (isinf(ts)) infinite = true;
           else dev = df_add(dev, ts);
@@ -299,7 +295,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
         if (lane == 0) atomicAdd(E.loss, (double)sse);
       }
       if (MODE == kFwdScan && row_on)
-        E.parts[(size_t)(n0 / BN) * E.rows_valid + m] =
+        E.parts[((size_t)(n0 / BN) * 2 + half) * E.rows_valid + m] =
             infinite ? __longlong_as_double(0x7ff0000000000000LL) : (double)dev.hi + (double)dev.lo;
     }
   }
@@ -310,7 +306,9 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
   if (warp == kMmaWarp) tmem_dealloc(tmem_base, S::kTmemCols);
 }
 
-// theta [rows][5] -> X0 [M][128] and X0^T [128][M] (BF16), normalised to the box.
+// theta [rows][5] -> X0 [M][128] and X0^T [128][M] (BF16), normalised to the
+// box.  Only columns 0-7 of X0 and rows 0-4 of X0^T are written: the padding
+// is zeroed once when the buffers are made.
 __global__ void mlp_input_kernel(const float* __restrict__ theta, int rows, int M, float4 c0, float c4, float4 h0,
                                  float h4, __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ xt) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,12 +322,27 @@ __global__ void mlp_input_kernel(const float* __restrict__ theta, int rows, int 
     u[3] = (th[3] - c0.w) / h0.w;
     u[4] = (th[4] - c4) / h4;
   }
-  __nv_bfloat16* row = x + (size_t)m * kInPad;
-  for (int k = 0; k < kInPad; ++k) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(k < kIn ? u[k] : 0.f);
-    row[k] = b;
-    if (xt) xt[(size_t)k * M + m] = b;
+  *reinterpret_cast<uint4*>(x + (size_t)m * kInPad) =
+      make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], 0.f), 0u);
+  if (xt)
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) xt[(size_t)k * M + m] = __float2bfloat16_rn(u[k]);
+}
+
+// Per-bin constants of the scan epilogue (from the standardization, the output
+// bias and the data): {m_j + s_j b_j, s_j, n_j, n_j ln n_j - n_j}; masked bins
+// and padding columns {0, 0, 0, -1} (exp(0) - 1 = 0).
+__global__ void scan_consts_kernel(const float* __restrict__ mean, const float* __restrict__ stdv,
+                                   const float* __restrict__ bias, const float2* __restrict__ nb, int n, int n_pad,
+                                   float4* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_pad) return;
+  float4 c = make_float4(0.f, 0.f, 0.f, -1.f);
+  if (j < n && nb[j].x >= 0.f) {
+    const float nj = nb[j].x;
+    c = make_float4(fmaf(stdv[j], bias[j], mean[j]), stdv[j], nj, nj > 0.f ? nj * logf(nj) - nj : 0.f);
   }
+  out[j] = c;
 }
 
 // db[r] = sum_m dZ^T[r][m]: one warp per row.
@@ -394,12 +407,15 @@ __global__ void cast_weights_kernel(const float* __restrict__ w, int out, int in
   wt_bf[(size_t)c * out + o] = b;
 }
 
-// Training targets: log(mu_sig + b) in place ([rows][ld], columns < n valid; padding = 0).
-__global__ void log_counts_kernel(float* __restrict__ t, long long rows, int n, int ld, const double* __restrict__ b64) {
+// Training targets: dst [rows][ld] = log(mu_sig + b) from src [rows][n]
+// (columns >= n of dst: 0).
+__global__ void log_counts_kernel(const float* __restrict__ src, long long rows, int n, int ld,
+                                  const double* __restrict__ b64, float* __restrict__ dst) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * ld) return;
+  const long long r = i / ld;
   const int j = (int)(i % ld);
-  t[i] = j < n ? logf(fmaxf(t[i] + (float)b64[j], 1e-30f)) : 0.f;
+  dst[i] = j < n ? logf(fmaxf(src[r * n + j] + (float)b64[j], 1e-30f)) : 0.f;
 }
 
 // Per-column sums and sums of squares (FP64) over rows, for the standardization.
@@ -437,13 +453,15 @@ __global__ void standardize_kernel(float* __restrict__ t, long long rows, int ld
   if (j < n) t[i] = (t[i] - mean[j]) / stdv[j];
 }
 
+// -2 ln L = 2 sum of the per-tile deviance partials + the data constant.
+template <class T>
 __global__ void scan_reduce_kernel(const double* __restrict__ parts, int n_parts, int rows,
-                                   const double* __restrict__ c_data, double* __restrict__ out) {
+                                   const double* __restrict__ c_data, T* __restrict__ out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= rows) return;
   double s = 0.0;
   for (int t = 0; t < n_parts; ++t) s += parts[(size_t)t * rows + p];
-  out[p] = 2.0 * s + *c_data;
+  out[p] = (T)(2.0 * s + *c_data);
 }
 
 // Sobol points in Gray-code order (Antonov-Saleev): point i is the xor of the
@@ -467,6 +485,111 @@ __global__ void sobol_kernel(const uint32_t* __restrict__ V, long long first, in
   out[2] = lo0.z + w0.z * (__uint2float_rn(x[2]) * s);
   out[3] = lo0.w + w0.w * (__uint2float_rn(x[3]) * s);
   out[4] = lo4 + w4 * (__uint2float_rn(x[4]) * s);
+}
+
+// The same points for a list of sequence indices.
+__global__ void sobol_gather_kernel(const uint32_t* __restrict__ V, const long long* __restrict__ index, int count,
+                                    float4 lo0, float lo4, float4 w0, float w4, float* __restrict__ theta) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const unsigned long long i = (unsigned long long)index[r];
+  unsigned long long gcode = i ^ (i >> 1);
+  uint32_t x[kIn] = {0u, 0u, 0u, 0u, 0u};
+  for (int k = 0; gcode != 0ull && k < 32; ++k, gcode >>= 1)
+    if (gcode & 1ull)
+#pragma unroll
+      for (int d = 0; d < kIn; ++d) x[d] ^= V[d * 32 + k];
+  const float s = 2.3283064365386963e-10f;
+  float* out = theta + (size_t)r * kIn;
+  out[0] = lo0.x + w0.x * (__uint2float_rn(x[0]) * s);
+  out[1] = lo0.y + w0.y * (__uint2float_rn(x[1]) * s);
+  out[2] = lo0.z + w0.z * (__uint2float_rn(x[2]) * s);
+  out[3] = lo0.w + w0.w * (__uint2float_rn(x[3]) * s);
+  out[4] = lo4 + w4 * (__uint2float_rn(x[4]) * s);
+}
+
+// Radix selection of the k-th smallest non-negative float (whose bit pattern
+// orders like its value): histogram of the high 16 bits, then of the low 16
+// bits among the values with a given high half.
+__global__ void hist_hi_kernel(const float* __restrict__ v, long long n, unsigned* __restrict__ hist) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    atomicAdd(hist + (__float_as_uint(v[i]) >> 16), 1u);
+}
+
+__global__ void hist_lo_kernel(const float* __restrict__ v, long long n, unsigned hi, unsigned* __restrict__ hist) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned b = __float_as_uint(v[i]);
+    if ((b >> 16) == hi) atomicAdd(hist + (b & 0xFFFFu), 1u);
+  }
+}
+
+__device__ __forceinline__ int cell_of(const float* th, float4 lo0, float lo4, float4 w0, float w4, int cpd) {
+  const float u[kIn] = {(th[0] - lo0.x) / w0.x, (th[1] - lo0.y) / w0.y, (th[2] - lo0.z) / w0.z, (th[3] - lo0.w) / w0.w,
+                        (th[4] - lo4) / w4};
+  int c = 0;
+  for (int d = kIn - 1; d >= 0; --d) {
+    int k = (int)floorf(u[d] * (float)cpd);
+    k = k < 0 ? 0 : (k >= cpd ? cpd - 1 : k);
+    c = c * cpd + k;
+  }
+  return c;
+}
+
+// Indices (first + i) of the scan points to re-evaluate exactly: surrogate
+// value v <= keep, or v > skip and v - margin[cell] <= bound (margin +inf:
+// always, -inf: never).  The cell is computed from the point itself.
+__global__ void select_kernel(const float* __restrict__ v, const uint32_t* __restrict__ V, long long first, long long n,
+                              float keep, float skip, const float* __restrict__ margin, float bound, int cpd,
+                              float4 lo0, float lo4, float4 w0, float w4, long long* __restrict__ out,
+                              unsigned long long* __restrict__ count, long long cap) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float vi = v[i];
+    bool take = vi <= keep;
+    if (!take && vi > skip && margin != nullptr) {
+      const unsigned long long idx = (unsigned long long)(first + i);
+      unsigned long long gcode = idx ^ (idx >> 1);
+      uint32_t x[kIn] = {0u, 0u, 0u, 0u, 0u};
+      for (int k = 0; gcode != 0ull && k < 32; ++k, gcode >>= 1)
+        if (gcode & 1ull)
+          for (int d = 0; d < kIn; ++d) x[d] ^= V[d * 32 + k];
+      const float s = 2.3283064365386963e-10f;
+      const float th[kIn] = {lo0.x + w0.x * (__uint2float_rn(x[0]) * s), lo0.y + w0.y * (__uint2float_rn(x[1]) * s),
+                             lo0.z + w0.z * (__uint2float_rn(x[2]) * s), lo0.w + w0.w * (__uint2float_rn(x[3]) * s),
+                             lo4 + w4 * (__uint2float_rn(x[4]) * s)};
+      take = vi - margin[cell_of(th, lo0, lo4, w0, w4, cpd)] <= bound;
+    }
+    if (take) {
+      const unsigned long long slot = atomicAdd(count, 1ull);
+      if ((long long)slot < cap) out[slot] = first + i;
+    }
+  }
+}
+
+// Minimum of non-negative values (their bit patterns order like the values)
+// and the first index that attains it.
+template <class T>
+__global__ void min_bits_kernel(const T* __restrict__ v, long long n, unsigned long long* __restrict__ best) {
+  unsigned long long m = ~0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long b = sizeof(T) == 8 ? (unsigned long long)__double_as_longlong((double)v[i])
+                                                : (unsigned long long)__float_as_uint((float)v[i]);
+    m = b < m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+    m = x < m ? x : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(best, m);
+}
+
+template <class T>
+__global__ void argmin_kernel(const T* __restrict__ v, long long n, const unsigned long long* __restrict__ best,
+                              unsigned long long* __restrict__ index) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long b = sizeof(T) == 8 ? (unsigned long long)__double_as_longlong((double)v[i])
+                                                : (unsigned long long)__float_as_uint((float)v[i]);
+    if (b == *best) atomicMin(index, (unsigned long long)i);
+  }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -588,6 +711,7 @@ struct srw_surrogate_ctx {
   SurrogateLayer L[4];
   float* mean = nullptr;  // per-bin standardization of log mu
   float* stdv = nullptr;
+  float4* binc = nullptr;  // per-bin constants of the scan epilogue
   int stats_ready = 0;
   long long adam_t = 0;
   unsigned* d_status = nullptr;
@@ -621,6 +745,8 @@ void sfree(T*& p) {
   if (p) cudaFree(p);
   p = nullptr;
 }
+
+int round_up(long long x, int m) { return (int)((x + m - 1) / m * m); }
 
 void free_batch(SurrogateBatch* B) {
   sfree(B->x); sfree(B->xt); sfree(B->dy); sfree(B->dyt); sfree(B->y); sfree(B->parts); sfree(B->loss);
@@ -685,11 +811,12 @@ srw_status get_batch(srw_surrogate s, int M, bool train, SurrogateBatch** out) {
   const int H = srw::kHidden, NO = s->n_out_pad;
   cudaError_t e = salloc(&B->x, (size_t)M * srw::kInPad);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = salloc(&B->h[k], (size_t)M * H);
-  if (e == cudaSuccess) e = salloc(&B->y, (size_t)M * NO);
-  if (e == cudaSuccess) e = salloc(&B->parts, (size_t)(NO / 256) * M);
+  if (e == cudaSuccess) e = salloc(&B->parts, (size_t)(NO / 256) * 2 * M);
+  if (e == cudaSuccess) e = cudaMemset(B->x, 0, sizeof(__nv_bfloat16) * (size_t)M * srw::kInPad);
   if (e == cudaSuccess) e = salloc(&B->loss, 1);
   if (train) {
     if (e == cudaSuccess) e = salloc(&B->xt, (size_t)M * srw::kInPad);
+    if (e == cudaSuccess) e = cudaMemset(B->xt, 0, sizeof(__nv_bfloat16) * (size_t)M * srw::kInPad);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = salloc(&B->ht[k], (size_t)M * H);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = salloc(&B->gz[k], (size_t)M * H);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = salloc(&B->dz[k], (size_t)M * H);
@@ -723,9 +850,7 @@ srw_status get_batch(srw_surrogate s, int M, bool train, SurrogateBatch** out) {
   if (e == cudaSuccess) {
     srw::EpiArgs E = epi0(M, NO, M, s->n_out);
     E.bias = s->L[3].b;
-    E.mean = s->mean;
-    E.stdv = s->stdv;
-    E.nb = reinterpret_cast<const float2*>(s->h->d_nb2);
+    E.binc = s->binc;
     E.parts = B->parts;
     e = prep(B->fwd_scan, B->h[2], s->L[3].w_bf, M, NO, H, srw::kFwdScan, 256, E);
   }
@@ -795,8 +920,8 @@ cudaError_t forward_hidden(srw_surrogate s, const float* theta, int rows, Surrog
 // t [M][n_out_pad] (FP32, device); gradients land in L[l].gw / gb, the summed
 // squared error in B->loss.
 cudaError_t fit_pass(srw_surrogate s, const float* theta, const float* targets, int rows, SurrogateBatch* B,
-                     cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(B->loss, 0, sizeof(double), st);
+                     cudaStream_t st, bool reset_loss = true) {
+  cudaError_t e = reset_loss ? cudaMemsetAsync(B->loss, 0, sizeof(double), st) : cudaSuccess;
   if (e == cudaSuccess) e = forward_hidden(s, theta, rows, B, true, st);
   if (e != cudaSuccess) return e;
   Gemm g = B->fwd[3];
@@ -841,6 +966,42 @@ cudaError_t adam_update(srw_surrogate s, float lr, float beta1, float beta2, flo
   return cudaGetLastError();
 }
 
+constexpr int kScanChunk = 1 << 20;  // points per surrogate launch chain in scans
+
+// Surrogate -2 ln L of P points (device theta), written as T (double or float).
+template <class T>
+srw_status loglik_device(srw_surrogate s, const float* theta, long long P, T* out, cudaStream_t st) {
+  srw::scan_consts_kernel<<<(s->n_out_pad + 255) / 256, 256, 0, st>>>(
+      s->mean, s->stdv, s->L[3].b, reinterpret_cast<const float2*>(s->h->d_nb2), s->n_out, s->n_out_pad, s->binc);
+  for (long long off = 0; off < P; off += kScanChunk) {
+    const int rows = (int)std::min<long long>(kScanChunk, P - off);
+    SurrogateBatch* B = nullptr;
+    srw_status r = get_batch(s, round_up(rows, srw::kBM) < 65536 ? round_up(rows, srw::kBM) : round_up(rows, 65536), false, &B);
+    if (r != SRW_OK) return r;
+    cudaError_t e = forward_hidden(s, theta + off * 5, rows, B, false, st);
+    if (e == cudaSuccess) {
+      Gemm g = B->fwd_scan;
+      g.E.rows_valid = rows;
+      e = srw::run_gemm(g, s->sm_count, s->d_status, st);
+    }
+    if (e == cudaSuccess) {
+      srw::scan_reduce_kernel<T><<<(rows + 255) / 256, 256, 0, st>>>(B->parts, s->n_out_pad / 256 * 2, rows, s->h->d_cdata,
+                                                                   out + off);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return scuda(s, e, "surrogate likelihood");
+  }
+  return SRW_OK;
+}
+
+void box_of(srw_surrogate s, float4* lo0, float* lo4, float4* w0, float* w4) {
+  *lo0 = make_float4(s->centre[0] - s->half[0], s->centre[1] - s->half[1], s->centre[2] - s->half[2],
+                     s->centre[3] - s->half[3]);
+  *lo4 = s->centre[4] - s->half[4];
+  *w0 = make_float4(2.f * s->half[0], 2.f * s->half[1], 2.f * s->half[2], 2.f * s->half[3]);
+  *w4 = 2.f * s->half[4];
+}
+
 srw_status check_status(srw_surrogate s, cudaStream_t st) {
   unsigned v = 0;
   S_CUDA(s, cudaMemcpyAsync(&v, s->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "status read");
@@ -849,8 +1010,6 @@ srw_status check_status(srw_surrogate s, cudaStream_t st) {
   if (v & srw::kStatusTimeout) return sfail(s, SRW_ETIMEOUT, "a bounded device wait expired; the kernel aborted");
   return SRW_OK;
 }
-
-int round_up(long long x, int m) { return (int)((x + m - 1) / m * m); }
 
 srw_status upload_weights(srw_surrogate s, const float* const* w) {
   const int real_in[4] = {srw::kIn, srw::kHidden, srw::kHidden, srw::kHidden};
@@ -928,6 +1087,7 @@ srw_status srw_surrogate_create(srw_handle h, const float* centre, const float* 
   }
   if (e == cudaSuccess) e = salloc(&s->mean, s->n_out_pad);
   if (e == cudaSuccess) e = salloc(&s->stdv, s->n_out_pad);
+  if (e == cudaSuccess) e = salloc(&s->binc, s->n_out_pad);
   if (e == cudaSuccess) {  // identity standardization until training sets it
     std::vector<float> z(s->n_out_pad, 0.f), o(s->n_out_pad, 1.f);
     e = cudaMemcpy(s->mean, z.data(), sizeof(float) * z.size(), cudaMemcpyHostToDevice);
@@ -987,7 +1147,12 @@ srw_status srw_surrogate_forward(srw_surrogate s, const float* theta, int P, flo
   float* d_th = nullptr;
   S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
-  cudaError_t e = forward_hidden(s, d_th, P, B, false, s->stream);
+  cudaError_t e = cudaSuccess;
+  if (!B->y) {  // the FP32 output buffer exists only for this hook
+    e = salloc(&B->y, (size_t)M * s->n_out_pad);
+    B->fwd_out.E.out_f32 = B->y;
+  }
+  if (e == cudaSuccess) e = forward_hidden(s, d_th, P, B, false, s->stream);
   if (e == cudaSuccess) {
     Gemm g = B->fwd_out;
     g.E.rows_valid = P;
@@ -1069,6 +1234,437 @@ srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const f
   return check_status(s, s->stream);
 }
 
+srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* o,
+                             float* epoch_loss) {
+  if (!s || !theta || !o || n < 1) return SRW_EINVAL;
+  if (o->batch < srw::kBM || o->batch % srw::kBM || o->epochs < 0 || !(o->lr > 0.f) || !(o->lr_final >= 0.f))
+    return sfail(s, SRW_EINVAL, "batch must be a positive multiple of 128; epochs >= 0; lr > 0");
+  if (o->precision < SRW_FP32 || o->precision > SRW_FP16X3) return sfail(s, SRW_EINVAL, "bad precision");
+  for (long long q = 0; q < n * 5; ++q)
+    if (!std::isfinite(theta[q])) return sfail(s, SRW_EINVAL, "theta must be finite");
+  srw_ctx* h = s->h;
+  cudaStream_t st = s->stream;
+  const int M = o->batch, NO = s->n_out_pad, NR = s->n_out;
+  const long long steps = (n + M - 1) / M, n_pad = steps * M;
+  constexpr int kGen = 65536;  // training spectra per exact-path launch
+  float *d_th = nullptr, *d_t = nullptr, *d_tmp = nullptr;
+  double* d_stats = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    sfree(d_th);
+    sfree(d_t);
+    sfree(d_tmp);
+    sfree(d_stats);
+  };
+  cudaError_t e = salloc(&d_th, (size_t)n_pad * 5);
+  if (e == cudaSuccess) e = salloc(&d_t, (size_t)n_pad * NO);
+  if (e == cudaSuccess) e = salloc(&d_tmp, (size_t)kGen * NR);
+  if (e == cudaSuccess) e = salloc(&d_stats, 2 * (size_t)NO);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_th, 0, sizeof(float) * n_pad * 5, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_t, 0, sizeof(float) * n_pad * NO, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_stats, 0, sizeof(double) * 2 * NO, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_th, theta, sizeof(float) * n * 5, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return scuda(s, e, "training buffers");
+  }
+  // targets: log of the exact expected counts (signal of the exact path + background)
+  for (long long off = 0; off < n; off += kGen) {
+    const int cnt = (int)std::min<long long>(kGen, n - off);
+    const srw_status r = srw_spectrum_batch(h, d_th + off * 5, cnt, d_tmp, SRW_DEVICE, (srw_precision)o->precision, st);
+    if (r != SRW_OK) {
+      cleanup();
+      return sfail(s, r, std::string("exact spectra: ") + srw_last_error(h));
+    }
+    srw::log_counts_kernel<<<(unsigned)(((long long)cnt * NO + 255) / 256), 256, 0, st>>>(d_tmp, cnt, NR, NO, h->d_b64,
+                                                                                      d_t + off * NO);
+  }
+  // per-bin standardization over the training set
+  srw::colstats_kernel<<<dim3((NR + 255) / 256, (unsigned)((n + 4095) / 4096)), 256, 0, st>>>(d_t, n, NO, NR, d_stats,
+                                                                                          d_stats + NO);
+  srw::finish_stats_kernel<<<(NR + 255) / 256, 256, 0, st>>>(d_stats, d_stats + NO, n, NR, s->mean, s->stdv);
+  srw::standardize_kernel<<<(unsigned)((n * NO + 255) / 256), 256, 0, st>>>(d_t, n, NO, NR, s->mean, s->stdv);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    cleanup();
+    return scuda(s, e, "targets");
+  }
+  SurrogateBatch* B = nullptr;
+  srw_status r = get_batch(s, M, true, &B);
+  if (r != SRW_OK) {
+    cleanup();
+    return r;
+  }
+  const long long total = steps * o->epochs;
+  long long t = 0;
+  for (int ep = 0; ep < o->epochs; ++ep) {
+    e = cudaMemsetAsync(B->loss, 0, sizeof(double), st);
+    for (long long b = 0; b < steps && e == cudaSuccess; ++b, ++t) {
+      const int rows = (int)std::min<long long>(M, n - b * M);
+      const double frac = total > 1 ? (double)t / (double)(total - 1) : 0.0;
+      const float lr = (float)(o->lr_final + 0.5 * (o->lr - o->lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
+      e = fit_pass(s, d_th + b * M * 5, d_t + b * M * NO, rows, B, st, false);
+      if (e == cudaSuccess) e = adam_update(s, lr, 0.9f, 0.999f, 1e-8f, st);
+    }
+    double sse = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sse, B->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cleanup();
+      return scuda(s, e, "training");
+    }
+    // each step's error is already a mean over its own points: average the steps
+    if (epoch_loss) epoch_loss[ep] = (float)(sse / ((double)n * NR));
+  }
+  cleanup();
+  s->stats_ready = 1;
+  return check_status(s, st);
+}
+
+srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, double* out, int where, void* stream) {
+  if (!s || !theta || !out || P < 1) return SRW_EINVAL;
+  if (where != SRW_HOST && where != SRW_DEVICE) return sfail(s, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
+  cudaStream_t st = stream ? (cudaStream_t)stream : s->stream;
+  if (where == SRW_DEVICE) {
+    srw_status r = loglik_device<double>(s, theta, P, out, st);
+    if (r == SRW_OK && !stream) S_CUDA(s, cudaStreamSynchronize(st), "sync");
+    return r;
+  }
+  for (long long q = 0; q < (long long)P * 5; ++q)
+    if (!std::isfinite(theta[q])) return sfail(s, SRW_EINVAL, "theta must be finite");
+  float* d_th = nullptr;
+  double* d_out = nullptr;
+  S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, st), "alloc");
+  S_CUDA(s, cudaMallocAsync(&d_out, sizeof(double) * (size_t)P, st), "alloc");
+  S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, st), "upload");
+  srw_status r = loglik_device<double>(s, d_th, P, d_out, st);
+  if (r == SRW_OK)
+    S_CUDA(s, cudaMemcpyAsync(out, d_out, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, st), "download");
+  cudaFreeAsync(d_th, st);
+  cudaFreeAsync(d_out, st);
+  if (r != SRW_OK) return r;
+  return check_status(s, st);
+}
+
+srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long n_points, int precision,
+                                    double* best_value, long long* best_index, float* ms) {
+  if (!s || n_points < 1 || first < 0) return SRW_EINVAL;
+  cudaStream_t st = s->stream;
+  constexpr int kChunk = 65536;
+  float4 lo0, w0;
+  float lo4, w4;
+  box_of(s, &lo0, &lo4, &w0, &w4);
+  float* d_th = nullptr;
+  double *d_v = nullptr, *d_o = nullptr;
+  unsigned long long* d_best = nullptr;
+  S_CUDA(s, salloc(&d_th, (size_t)kChunk * 5), "alloc");
+  S_CUDA(s, salloc(&d_v, (size_t)n_points), "alloc");
+  S_CUDA(s, salloc(&d_o, (size_t)kChunk), "alloc");
+  S_CUDA(s, salloc(&d_best, 2), "alloc");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  srw_status r = SRW_OK;
+  for (long long off = 0; off < n_points && r == SRW_OK; off += kChunk) {
+    const int cnt = (int)std::min<long long>(kChunk, n_points - off);
+    srw::sobol_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(s->d_sobol, first + off, cnt, lo0, lo4, w0, w4, d_th);
+    // fixed input and output buffers: the exact path replays one captured graph per chunk size
+    r = srw_loglik(s->h, d_th, cnt, d_o, SRW_DEVICE, (srw_precision)precision, st);
+    if (r == SRW_OK && cudaMemcpyAsync(d_v + off, d_o, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      r = SRW_ECUDA;
+  }
+  const unsigned long long init[2] = {~0ull, ~0ull};
+  cudaMemcpyAsync(d_best, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  srw::min_bits_kernel<double><<<1024, 256, 0, st>>>(d_v, n_points, d_best);
+  srw::argmin_kernel<double><<<1024, 256, 0, st>>>(d_v, n_points, d_best, d_best + 1);
+  cudaEventRecord(e1, st);
+  unsigned long long res[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(res, d_best, sizeof(res), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  sfree(d_th);
+  sfree(d_v);
+  sfree(d_o);
+  sfree(d_best);
+  if (r != SRW_OK) return sfail(s, r, std::string("exact scan: ") + srw_last_error(s->h));
+  if (e != cudaSuccess) return scuda(s, e, "exact scan");
+  double v;
+  const long long bits = (long long)res[0];
+  std::memcpy(&v, &bits, sizeof(v));
+  if (best_value) *best_value = v;
+  if (best_index) *best_index = first + (long long)res[1];
+  if (ms) *ms = t;
+  return check_status(s, st);
+}
+
+namespace {
+
+// Exact -2 ln L of the points with the listed Sobol indices; returns the
+// minimum and the index of the point that attains it (index -1 if count = 0).
+srw_status exact_min_of(srw_surrogate s, const long long* d_idx, long long count, int precision, float4 lo0, float lo4,
+                        float4 w0, float w4, float* d_th, double* d_o, double* best_value, long long* best_index) {
+  cudaStream_t st = s->stream;
+  constexpr int kChunk = 65536;
+  *best_value = INFINITY;
+  *best_index = -1;
+  if (count <= 0) return SRW_OK;
+  double* d_ex = nullptr;
+  unsigned long long* d_best = nullptr;
+  S_CUDA(s, salloc(&d_ex, (size_t)count), "alloc");
+  S_CUDA(s, salloc(&d_best, 2), "alloc");
+  srw_status r = SRW_OK;
+  for (long long off = 0; off < count && r == SRW_OK; off += kChunk) {
+    const int cnt = (int)std::min<long long>(kChunk, count - off);
+    srw::sobol_gather_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(s->d_sobol, d_idx + off, cnt, lo0, lo4, w0, w4, d_th);
+    r = srw_loglik(s->h, d_th, cnt, d_o, SRW_DEVICE, (srw_precision)precision, st);
+    if (r == SRW_OK && cudaMemcpyAsync(d_ex + off, d_o, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      r = SRW_ECUDA;
+  }
+  unsigned long long best[2] = {~0ull, ~0ull};
+  cudaError_t e = cudaSuccess;
+  if (r == SRW_OK) {
+    e = cudaMemcpyAsync(d_best, best, sizeof(best), cudaMemcpyHostToDevice, st);
+    srw::min_bits_kernel<double><<<1024, 256, 0, st>>>(d_ex, count, d_best);
+    srw::argmin_kernel<double><<<1024, 256, 0, st>>>(d_ex, count, d_best, d_best + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best, d_best, sizeof(best), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(best_index, d_idx + best[1], sizeof(long long), cudaMemcpyDeviceToHost);
+  }
+  cudaStreamSynchronize(st);
+  sfree(d_ex);
+  sfree(d_best);
+  if (r != SRW_OK) return sfail(s, r, std::string("exact re-evaluation: ") + srw_last_error(s->h));
+  if (e != cudaSuccess) return scuda(s, e, "exact re-evaluation");
+  const long long bits = (long long)best[0];
+  std::memcpy(best_value, &bits, sizeof(double));
+  return SRW_OK;
+}
+
+}  // namespace
+
+srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* o, srw_scan_result* res) {
+  if (!s || !o || !res) return SRW_EINVAL;
+  if (o->n_points < 1 || o->first < 0 || !(o->keep_frac > 0.0 && o->keep_frac <= 1.0) || o->n_check < 0 ||
+      (o->n_check > 0 && !o->check_theta) || o->cells_per_dim < 1 || o->cells_per_dim > 16 || !(o->tol >= 0.0) ||
+      (o->rule != SRW_SCAN_FLAG_CELLS && o->rule != SRW_SCAN_ERROR_BARS) || !(o->margin_factor >= 1.0))
+    return sfail(s, SRW_EINVAL, "bad scan options");
+  std::memset(res, 0, sizeof(*res));
+  cudaStream_t st = s->stream;
+  const int cpd = o->cells_per_dim;
+  const int n_cells = cpd * cpd * cpd * cpd * cpd;
+  res->n_cells = n_cells;
+  float4 lo0, w0;
+  float lo4, w4;
+  box_of(s, &lo0, &lo4, &w0, &w4);
+  cudaEvent_t ev[5];
+  for (auto& x : ev) cudaEventCreate(&x);
+  cudaEventRecord(ev[0], st);
+  // ---- held-out check: both paths on the check points; per-cell largest |d|
+  std::vector<double> cmax(n_cells, -1.0);  // -1: no check point in the cell
+  if (o->n_check > 0) {
+    float* d_c = nullptr;
+    double *d_ex = nullptr, *d_su = nullptr;
+    S_CUDA(s, salloc(&d_c, (size_t)o->n_check * 5), "alloc");
+    S_CUDA(s, salloc(&d_ex, (size_t)o->n_check), "alloc");
+    S_CUDA(s, salloc(&d_su, (size_t)o->n_check), "alloc");
+    S_CUDA(s, cudaMemcpyAsync(d_c, o->check_theta, sizeof(float) * 5 * o->n_check, cudaMemcpyHostToDevice, st), "upload");
+    srw_status r = srw_loglik(s->h, d_c, o->n_check, d_ex, SRW_DEVICE, (srw_precision)o->precision, st);
+    if (r == SRW_OK) r = loglik_device<double>(s, d_c, o->n_check, d_su, st);
+    std::vector<double> ex(o->n_check), su(o->n_check);
+    if (r == SRW_OK) {
+      cudaMemcpyAsync(ex.data(), d_ex, sizeof(double) * o->n_check, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(su.data(), d_su, sizeof(double) * o->n_check, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+    }
+    sfree(d_c);
+    sfree(d_ex);
+    sfree(d_su);
+    if (r != SRW_OK) return r;
+    for (int i = 0; i < o->n_check; ++i) {
+      const float* th = o->check_theta + (size_t)i * 5;
+      const float u[5] = {(th[0] - lo0.x) / w0.x, (th[1] - lo0.y) / w0.y, (th[2] - lo0.z) / w0.z, (th[3] - lo0.w) / w0.w,
+                          (th[4] - lo4) / w4};
+      int c = 0;
+      for (int d = 4; d >= 0; --d) {
+        int k = (int)std::floor(u[d] * (float)cpd);
+        k = k < 0 ? 0 : (k >= cpd ? cpd - 1 : k);
+        c = c * cpd + k;
+      }
+      const double dd = std::isfinite(ex[i]) && std::isfinite(su[i]) ? std::fabs(su[i] - ex[i]) : INFINITY;
+      cmax[c] = std::max(cmax[c], dd);
+      res->check_max_abs_d = std::max(res->check_max_abs_d, dd);
+    }
+  }
+  for (int c = 0; c < n_cells; ++c)
+    if (o->n_check > 0 && (cmax[c] < 0.0 || cmax[c] > o->tol)) ++res->n_flagged_cells;
+  cudaEventRecord(ev[1], st);
+  // ---- surrogate values of every scan point
+  float* d_vals = nullptr;
+  float* d_th = nullptr;
+  double* d_o = nullptr;
+  S_CUDA(s, salloc(&d_vals, (size_t)o->n_points), "alloc scan values");
+  S_CUDA(s, salloc(&d_th, (size_t)kScanChunk * 5), "alloc");
+  S_CUDA(s, salloc(&d_o, 65536), "alloc");
+  auto cleanup = [&](unsigned* a, unsigned long long* b, long long* c, float* m) {
+    cudaStreamSynchronize(st);
+    sfree(d_vals);
+    sfree(d_th);
+    sfree(d_o);
+    sfree(a);
+    sfree(b);
+    sfree(c);
+    sfree(m);
+    for (auto& x : ev) cudaEventDestroy(x);
+  };
+  for (long long off = 0; off < o->n_points; off += kScanChunk) {
+    const int cnt = (int)std::min<long long>(kScanChunk, o->n_points - off);
+    srw::sobol_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(s->d_sobol, o->first + off, cnt, lo0, lo4, w0, w4, d_th);
+    const srw_status r = loglik_device<float>(s, d_th, cnt, d_vals + off, st);
+    if (r != SRW_OK) {
+      cleanup(nullptr, nullptr, nullptr, nullptr);
+      return r;
+    }
+  }
+  cudaEventRecord(ev[2], st);
+  // ---- threshold of the lowest keep_frac (exact radix selection on the float bits)
+  const long long k = std::max<long long>(1, (long long)std::ceil(o->keep_frac * (double)o->n_points));
+  unsigned* d_hist = nullptr;
+  unsigned long long* d_cnt = nullptr;
+  long long* d_idx = nullptr;
+  float* d_margin = nullptr;
+  S_CUDA(s, salloc(&d_hist, 65536), "alloc");
+  S_CUDA(s, salloc(&d_cnt, 3), "alloc");
+  S_CUDA(s, salloc(&d_idx, (size_t)o->n_points), "alloc index list");
+  S_CUDA(s, salloc(&d_margin, (size_t)n_cells), "alloc");
+  std::vector<unsigned> hist(65536);
+  S_CUDA(s, cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * 65536, st), "zero");
+  srw::hist_hi_kernel<<<1024, 256, 0, st>>>(d_vals, o->n_points, d_hist);
+  S_CUDA(s, cudaMemcpyAsync(hist.data(), d_hist, sizeof(unsigned) * 65536, cudaMemcpyDeviceToHost, st), "hist");
+  S_CUDA(s, cudaStreamSynchronize(st), "sync");
+  long long cum = 0;
+  unsigned hi = 0;
+  for (; hi < 65535; ++hi) {
+    if (cum + hist[hi] >= k) break;
+    cum += hist[hi];
+  }
+  S_CUDA(s, cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * 65536, st), "zero");
+  srw::hist_lo_kernel<<<1024, 256, 0, st>>>(d_vals, o->n_points, hi, d_hist);
+  S_CUDA(s, cudaMemcpyAsync(hist.data(), d_hist, sizeof(unsigned) * 65536, cudaMemcpyDeviceToHost, st), "hist");
+  S_CUDA(s, cudaStreamSynchronize(st), "sync");
+  unsigned lo = 0;
+  for (; lo < 65535; ++lo) {
+    if (cum + hist[lo] >= k) break;
+    cum += hist[lo];
+  }
+  const unsigned tbits = (hi << 16) | lo;
+  float thresh;
+  std::memcpy(&thresh, &tbits, sizeof(thresh));
+  res->n_kept = cum + hist[lo];
+  // per-cell margins: SRW_SCAN_FLAG_CELLS keeps whole flagged cells (+inf);
+  // SRW_SCAN_ERROR_BARS uses margin_factor x max(held-out |d|, tol), +inf where
+  // a cell holds no check point
+  std::vector<float> margin(n_cells);
+  for (int c = 0; c < n_cells; ++c) {
+    const bool flagged = cmax[c] < 0.0 || cmax[c] > o->tol;
+    if (o->rule == SRW_SCAN_FLAG_CELLS) margin[c] = flagged && o->n_check > 0 ? INFINITY : -INFINITY;
+    else margin[c] = cmax[c] < 0.0 ? INFINITY : (float)(o->margin_factor * std::max(cmax[c], o->tol));
+  }
+  S_CUDA(s, cudaMemcpyAsync(d_margin, margin.data(), sizeof(float) * n_cells, cudaMemcpyHostToDevice, st), "upload");
+  // surrogate minimum (for the report)
+  const unsigned long long init3[3] = {0ull, ~0ull, ~0ull};
+  S_CUDA(s, cudaMemcpyAsync(d_cnt, init3, sizeof(init3), cudaMemcpyHostToDevice, st), "init");
+  srw::min_bits_kernel<float><<<1024, 256, 0, st>>>(d_vals, o->n_points, d_cnt + 1);
+  // pass 1: the lowest keep_frac (+ whole flagged cells under SRW_SCAN_FLAG_CELLS)
+  const bool cells = o->rule == SRW_SCAN_FLAG_CELLS;
+  srw::select_kernel<<<2048, 256, 0, st>>>(d_vals, s->d_sobol, o->first, o->n_points, thresh, thresh,
+                                           cells ? d_margin : nullptr, 0.f, cpd, lo0, lo4, w0, w4, d_idx, d_cnt,
+                                           o->n_points);
+  unsigned long long sel[2] = {0, 0};
+  S_CUDA(s, cudaMemcpyAsync(sel, d_cnt, sizeof(sel), cudaMemcpyDeviceToHost, st), "count");
+  S_CUDA(s, cudaStreamSynchronize(st), "sync");
+  {
+    const unsigned bsur = (unsigned)sel[1];
+    float f;
+    std::memcpy(&f, &bsur, sizeof(f));
+    res->surrogate_min = f;
+  }
+  long long n_sel = std::min<long long>((long long)sel[0], o->n_points);
+  cudaEventRecord(ev[3], st);
+  double best = INFINITY;
+  long long best_index = -1;
+  srw_status r = exact_min_of(s, d_idx, n_sel, o->precision, lo0, lo4, w0, w4, d_th, d_o, &best, &best_index);
+  if (r == SRW_OK && !cells) {
+    // pass 2: points outside pass 1 that could still beat the best exact value
+    // within their cell's error bar
+    S_CUDA(s, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st), "zero");
+    srw::select_kernel<<<2048, 256, 0, st>>>(d_vals, s->d_sobol, o->first, o->n_points, -1.f, thresh, d_margin,
+                                             (float)best, cpd, lo0, lo4, w0, w4, d_idx, d_cnt, o->n_points);
+    unsigned long long n2 = 0;
+    S_CUDA(s, cudaMemcpyAsync(&n2, d_cnt, sizeof(n2), cudaMemcpyDeviceToHost, st), "count");
+    S_CUDA(s, cudaStreamSynchronize(st), "sync");
+    res->n_rescued = std::min<long long>((long long)n2, o->n_points);
+    double b2 = INFINITY;
+    long long i2 = -1;
+    r = exact_min_of(s, d_idx, res->n_rescued, o->precision, lo0, lo4, w0, w4, d_th, d_o, &b2, &i2);
+    if (b2 < best || (b2 == best && i2 >= 0 && i2 < best_index)) {
+      best = b2;
+      best_index = i2;
+    }
+    n_sel += res->n_rescued;
+  }
+  cudaEventRecord(ev[4], st);
+  cudaStreamSynchronize(st);
+  float t[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+  cleanup(d_hist, d_cnt, d_idx, d_margin);
+  if (r != SRW_OK) return r;
+  res->n_selected = n_sel;
+  res->ms_check = t[0];
+  res->ms_surrogate = t[1];
+  res->ms_select = t[2];
+  res->ms_exact = t[3];
+  res->best_value = best;
+  res->best_index = best_index;
+  if (best_index >= 0) {  // the point itself, from its sequence index (host, same construction)
+    uint32_t V[5 * 32];
+    sobol_directions(V);
+    unsigned long long gcode = (unsigned long long)best_index ^ ((unsigned long long)best_index >> 1);
+    uint32_t x[5] = {0, 0, 0, 0, 0};
+    for (int kk = 0; gcode && kk < 32; ++kk, gcode >>= 1)
+      if (gcode & 1ull)
+        for (int d = 0; d < 5; ++d) x[d] ^= V[d * 32 + kk];
+    const float lo5[5] = {lo0.x, lo0.y, lo0.z, lo0.w, lo4}, w5[5] = {w0.x, w0.y, w0.z, w0.w, w4};
+    for (int d = 0; d < 5; ++d) res->best_theta[d] = lo5[d] + w5[d] * ((float)x[d] * 2.3283064365386963e-10f);
+  }
+  return check_status(s, st);
+}
+
+srw_status srw_surrogate_sobol(srw_surrogate s, long long first, int count, float* theta) {
+  if (!s || !theta || count < 1 || first < 0) return SRW_EINVAL;
+  float4 lo0, w0;
+  float lo4, w4;
+  box_of(s, &lo0, &lo4, &w0, &w4);
+  float* d = nullptr;
+  S_CUDA(s, salloc(&d, (size_t)count * 5), "alloc");
+  srw::sobol_kernel<<<(count + 255) / 256, 256, 0, s->stream>>>(s->d_sobol, first, count, lo0, lo4, w0, w4, d);
+  cudaError_t e = cudaMemcpyAsync(theta, d, sizeof(float) * 5 * (size_t)count, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  sfree(d);
+  if (e != cudaSuccess) return scuda(s, e, "sobol points");
+  return SRW_OK;
+}
+
+srw_status srw_surrogate_get_standardization(srw_surrogate s, float* mean, float* stdv) {
+  if (!s || !mean || !stdv) return SRW_EINVAL;
+  S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
+  S_CUDA(s, cudaMemcpy(mean, s->mean, sizeof(float) * s->n_out, cudaMemcpyDeviceToHost), "read");
+  S_CUDA(s, cudaMemcpy(stdv, s->stdv, sizeof(float) * s->n_out, cudaMemcpyDeviceToHost), "read");
+  return SRW_OK;
+}
+
 const char* srw_surrogate_last_error(srw_surrogate s) { return s ? s->err.c_str() : "NULL surrogate"; }
 
 srw_status srw_surrogate_destroy(srw_surrogate s) {
@@ -1082,6 +1678,7 @@ srw_status srw_surrogate_destroy(srw_surrogate s) {
   }
   sfree(s->mean);
   sfree(s->stdv);
+  sfree(s->binc);
   sfree(s->d_status);
   sfree(s->d_sobol);
   if (s->stream) cudaStreamDestroy(s->stream);

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libsrw.so")
 SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOUT, SRW_EUNSUPPORTED = range(8)
 SRW_HOST, SRW_DEVICE = 0, 1
 SRW_FP32, SRW_BF16, SRW_BF16X3, SRW_FP16X3 = 0, 1, 2, 3
+SRW_SCAN_FLAG_CELLS, SRW_SCAN_ERROR_BARS = 0, 1
 PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3, "fp16x3": SRW_FP16X3}
 
 # Entry points declared in include/srw.h (checked by the test-suite).
@@ -29,7 +30,8 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_group_autotune", "srw_group_set_schedule", "srw_group_schedule", "srw_group_profile", "srw_group_profile_read",
            "srw_group_last_error", "srw_group_destroy", "srw_surrogate_create", "srw_surrogate_set_weights",
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
-           "srw_surrogate_last_error", "srw_surrogate_destroy")
+           "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
+           "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization")
 
 
 class SrwError(RuntimeError):
@@ -60,6 +62,27 @@ class _Info(ctypes.Structure):
 
 
 _lib = None
+
+
+class _FitOpts(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("epochs", ctypes.c_int), ("lr", ctypes.c_float), ("lr_final", ctypes.c_float),
+                ("precision", ctypes.c_int)]
+
+
+class _ScanOpts(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_longlong), ("n_points", ctypes.c_longlong), ("keep_frac", ctypes.c_double),
+                ("check_theta", ctypes.c_void_p), ("n_check", ctypes.c_int), ("tol", ctypes.c_double),
+                ("cells_per_dim", ctypes.c_int), ("precision", ctypes.c_int), ("rule", ctypes.c_int),
+                ("margin_factor", ctypes.c_double)]
+
+
+class _ScanResult(ctypes.Structure):
+    _fields_ = [("best_value", ctypes.c_double), ("best_index", ctypes.c_longlong), ("best_theta", ctypes.c_float * 5),
+                ("surrogate_min", ctypes.c_double), ("n_kept", ctypes.c_longlong), ("n_selected", ctypes.c_longlong),
+                ("n_rescued", ctypes.c_longlong),
+                ("n_cells", ctypes.c_int), ("n_flagged_cells", ctypes.c_int), ("check_max_abs_d", ctypes.c_double),
+                ("ms_check", ctypes.c_float), ("ms_surrogate", ctypes.c_float), ("ms_select", ctypes.c_float),
+                ("ms_exact", ctypes.c_float)]
 
 
 def lib():
@@ -108,6 +131,14 @@ def lib():
         L.srw_surrogate_forward.argtypes = [vp, vp, ip, vp]
         L.srw_surrogate_gradients.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
         L.srw_surrogate_train_step.argtypes = [vp, vp, vp, ip, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+        L.srw_surrogate_fit.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(_FitOpts), vp]
+        L.srw_surrogate_loglik.argtypes = [vp, vp, ip, vp, ip, vp]
+        L.srw_surrogate_scan.argtypes = [vp, ctypes.POINTER(_ScanOpts), ctypes.POINTER(_ScanResult)]
+        L.srw_surrogate_scan_exact.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong, ip,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                               ctypes.POINTER(ctypes.c_float)]
+        L.srw_surrogate_sobol.argtypes = [vp, ctypes.c_longlong, ip, vp]
+        L.srw_surrogate_get_standardization.argtypes = [vp, vp, vp]
         L.srw_surrogate_last_error.argtypes = [vp]
         L.srw_surrogate_last_error.restype = ctypes.c_char_p
         L.srw_surrogate_destroy.argtypes = [vp]
@@ -575,6 +606,58 @@ class Surrogate:
 
     def train_step(self, theta, targets, lr):
         return srw_surrogate_train_step(self.handle, theta, targets, lr)
+
+    def fit(self, theta, epochs, batch=8192, lr=1e-3, lr_final=1e-5, precision=None):
+        """Train on the exact path's spectra at theta (host [n, 5]); returns the per-epoch losses."""
+        th = _f32(theta).reshape(-1, 5)
+        o = _FitOpts(int(batch), int(epochs), float(lr), float(lr_final),
+                     int(SRW_FP16X3 if precision is None else precision))
+        losses = np.zeros(max(1, int(epochs)), dtype=np.float32)
+        _scheck(lib().srw_surrogate_fit(self.handle, th.ctypes.data, th.shape[0], ctypes.byref(o), losses.ctypes.data),
+                self.handle)
+        return losses[:int(epochs)]
+
+    def loglik(self, theta, out=None, stream=None):
+        """Surrogate -2 ln L (host theta -> numpy; CUDA tensors -> written into out)."""
+        if _is_device(theta):
+            P = theta.numel() // 5
+            _scheck(lib().srw_surrogate_loglik(self.handle, ctypes.c_void_p(theta.data_ptr()), P,
+                                               ctypes.c_void_p(out.data_ptr()), SRW_DEVICE, _stream(stream)),
+                    self.handle)
+            return out
+        th = _f32(theta).reshape(-1, 5)
+        res = np.empty(th.shape[0], dtype=np.float64)
+        _scheck(lib().srw_surrogate_loglik(self.handle, th.ctypes.data, th.shape[0], res.ctypes.data, SRW_HOST, None),
+                self.handle)
+        return res
+
+    def scan(self, n_points, first=0, keep_frac=0.01, check_theta=None, tol=0.05, cells_per_dim=4, precision=None,
+             rule=SRW_SCAN_FLAG_CELLS, margin_factor=2.0):
+        chk = None if check_theta is None else _f32(check_theta).reshape(-1, 5)
+        o = _ScanOpts(int(first), int(n_points), float(keep_frac), chk.ctypes.data if chk is not None else None,
+                      0 if chk is None else chk.shape[0], float(tol), int(cells_per_dim),
+                      int(SRW_FP16X3 if precision is None else precision), int(rule), float(margin_factor))
+        r = _ScanResult()
+        _scheck(lib().srw_surrogate_scan(self.handle, ctypes.byref(o), ctypes.byref(r)), self.handle)
+        return {name: (list(getattr(r, name)) if name == "best_theta" else getattr(r, name)) for name, _ in r._fields_}
+
+    def scan_exact(self, n_points, first=0, precision=None):
+        v, i, ms = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_float()
+        _scheck(lib().srw_surrogate_scan_exact(self.handle, int(first), int(n_points),
+                                               int(SRW_FP16X3 if precision is None else precision), ctypes.byref(v),
+                                               ctypes.byref(i), ctypes.byref(ms)), self.handle)
+        return {"best_value": v.value, "best_index": i.value, "ms": ms.value}
+
+    def sobol(self, first, count):
+        out = np.empty((int(count), 5), dtype=np.float32)
+        _scheck(lib().srw_surrogate_sobol(self.handle, int(first), int(count), out.ctypes.data), self.handle)
+        return out
+
+    def standardization(self):
+        m = np.empty(self.n_out, dtype=np.float32)
+        sd = np.empty(self.n_out, dtype=np.float32)
+        _scheck(lib().srw_surrogate_get_standardization(self.handle, m.ctypes.data, sd.ctypes.data), self.handle)
+        return m, sd
 
     def close(self):
         if self.handle:

@@ -134,3 +134,91 @@ def test_training_reduces_the_loss(sur):
         last = s.train_step(theta, targets, 1e-3)
     assert last < 0.5 * first, (first, last)
     s.set_weights(params)
+
+
+# ---------------------------------------------------------------- Sobol points
+def test_sobol_points_match_oracle(sur):
+    from oracle.sobol import sobol_points
+    s, _ = sur
+    got = s.sobol(1000, 4096)
+    u = sobol_points(1000, 4096, 5)
+    want = (BOX_CENTRE - BOX_HALF).astype(np.float64) + 2.0 * BOX_HALF.astype(np.float64) * u
+    np.testing.assert_allclose(got, want, rtol=0, atol=4e-7)  # the FP32 map from [0, 1)
+
+
+# ---------------------------------------------------------------- training on the exact path
+@pytest.fixture(scope="module")
+def trained(srw, solar_lk):
+    params = init_weights(2048, seed=5)
+    s = srw.Surrogate(solar_lk, params, BOX_CENTRE, BOX_HALF)
+    theta = workloads.theta_box(1 << 20, 55)
+    losses = s.fit(theta, epochs=40, batch=4096, lr=2e-3, lr_final=2e-5)
+    yield s, losses
+    s.close()
+
+
+def test_fit_reduces_the_loss(trained):
+    s, losses = trained
+    print("epoch losses:", " ".join("%.2e" % x for x in losses))
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 1e-2 * losses[0], losses
+
+
+def test_surrogate_likelihood_epilogue(trained, solar_lk):
+    # The fused epilogue (exp, Poisson deviance, FP64 partial sums) against the
+    # oracle's formula applied to the same network output.  The epilogue works
+    # in FP32 on lm = log mu: rounding lm (|lm| <= ~10, 2^-24 relative) and the
+    # fast exponential (at most 2 + 1.17 |lm| ulp) give mu a relative error
+    # below 2e-6, and t = mu - n lm + (n ln n - n) adds FP32 roundings of its
+    # three terms; per point |d| <= 2 sum_j [2e-6 |mu_j - n_j| + 1.2e-7
+    # (mu_j + n_j |lm_j| + |n_j ln n_j - n_j|)] + 1e-3.
+    from oracle.mlp_oracle import data_constant, surrogate_neg2lnl
+    s, _ = trained
+    counts = workloads.load_counts("solar_set_4096")
+    theta = workloads.theta_box(257, 56)
+    y = s.forward(theta).astype(np.float64)
+    m, sd = s.standardization()
+    want = surrogate_neg2lnl(y, m, sd, counts, data_constant(counts))
+    got = s.loglik(theta)
+    lm = m + sd * y
+    mu = np.exp(lm)
+    c = np.where(counts > 0, counts * np.log(np.where(counts > 0, counts, 1.0)) - counts, 0.0)
+    bound = 2.0 * np.sum(2e-6 * np.abs(mu - counts) + 1.2e-7 * (mu + counts * np.abs(lm) + np.abs(c)), axis=1) + 1e-3
+    assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+
+
+def test_surrogate_against_exact_path(trained, solar_lk, srw):
+    s, _ = trained
+    theta = workloads.theta_box(2048, 57)
+    exact = solar_lk.loglik(theta, srw.SRW_FP16X3)
+    sur_v = s.loglik(theta)
+    d = np.abs(sur_v - exact)
+    rel = d / exact
+    print("surrogate vs exact: median |d| %.3g, 90%% %.3g, median rel %.3g, max rel %.3g" % (
+        np.median(d), np.quantile(d, 0.9), np.median(rel), rel.max()))
+    assert np.all(np.isfinite(sur_v))
+    assert np.median(rel) < 0.02
+
+
+@pytest.mark.parametrize("rule", ["cells", "error_bars"])
+def test_scan_finds_the_exact_minimum(trained, srw, rule):
+    # The gain of the trained network: the pre-screened scan must return the
+    # exact scan's minimum (same point, same exact value) while re-evaluating
+    # fewer points.  The literal rule re-evaluates every flagged cell; the
+    # error-bar rule re-evaluates only points that could still beat the best
+    # exact value within twice their cell's held-out error.
+    s, _ = trained
+    n = 1 << 21
+    ex = s.scan_exact(n)
+    check = workloads.theta_box(10000, 58)
+    code = srw.SRW_SCAN_FLAG_CELLS if rule == "cells" else srw.SRW_SCAN_ERROR_BARS
+    s.scan(n, check_theta=check, rule=code)  # first call makes the buffers
+    r = s.scan(n, keep_frac=0.01, check_theta=check, tol=0.05, cells_per_dim=4, rule=code, margin_factor=2.0)
+    t_pre = r["ms_check"] + r["ms_surrogate"] + r["ms_select"] + r["ms_exact"]
+    print("%s: exact scan %.2f ms; pre-screened %.2f ms (surrogate %.2f), re-evaluated %d of %d (%d flagged cells)"
+          % (rule, ex["ms"], t_pre, r["ms_surrogate"], r["n_selected"], n, r["n_flagged_cells"]))
+    assert r["n_selected"] >= r["n_kept"] >= 0.01 * n
+    assert r["best_index"] == ex["best_index"] and r["best_value"] == ex["best_value"]
+    if rule == "error_bars":
+        assert r["n_selected"] < 0.1 * n
+        assert t_pre < ex["ms"]
