@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-grouped", action="store_true", help="skip the 64-configuration grouped measurement")
     ap.add_argument("--grouped-only", action="store_true",
                     help="only the grouped measurement (for profiling its launch)")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--surrogate-only", action="store_true", help="only the learned-surrogate measurement")
+    ap.add_argument("--train-points", type=int, default=1_000_000, help="exact-path spectra the surrogate trains on")
+    ap.add_argument("--scan-points", type=int, default=100_000_000, help="Sobol points of the pre-screened scan")
     ap.add_argument("--groups", type=int, default=64, help="configurations of the grouped workload")
     ap.add_argument("--group-scale", type=float, default=1.0,
                     help="size factor of the grouped workload (profiling captures of a smaller case)")
@@ -283,6 +287,55 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
     return res
 
 
+# --------------------------------------------------------------------------- learned surrogate
+def surrogate_measurement(args, srw, workloads, lk, peaks, peak_src):
+    """The surrogate of the solar set: trained on exact-path spectra of points
+    uniform in the box, then a Sobol scan pre-screened by it (error-bar rule)
+    against the same scan on the exact path alone."""
+    import numpy as np
+    from workloads.mlp import BOX_CENTRE, BOX_HALF, init_weights
+
+    sg = srw.Surrogate(lk, init_weights(2048, seed=5), BOX_CENTRE, BOX_HALF)
+    theta = workloads.theta_box(args.train_points, 5)
+    epochs = 40
+    t0 = time.perf_counter()
+    losses = sg.fit(theta, epochs=epochs, batch=4096, lr=2e-3, lr_final=2e-5)
+    t_fit = time.perf_counter() - t0
+    check = workloads.theta_box(10000, 58)
+    exact_chk = lk.loglik(check, srw.SRW_FP16X3)
+    sur_chk = sg.loglik(check)
+    d = np.abs(sur_chk - exact_chk)
+    n = args.scan_points
+    rule = srw.SRW_SCAN_ERROR_BARS
+    sg.scan(min(n, 1 << 20), check_theta=check, rule=rule)  # buffers for the timed call
+    r = sg.scan(n, keep_frac=0.01, check_theta=check, tol=0.05, cells_per_dim=4, rule=rule, margin_factor=2.0)
+    ex = sg.scan_exact(n)
+    t_pre = r["ms_check"] + r["ms_surrogate"] + r["ms_select"] + r["ms_exact"]
+    flop_point = 2.0 * (5 * 256 + 256 * 256 * 2 + 256 * 2048)
+    achieved = flop_point * n / (r["ms_surrogate"] * 1e-3) / 1e12
+    sg.close()
+    return {
+        "workload": "solar_set_4096 surrogate, %d-point Sobol scan" % n,
+        "network": "5-256-256-256-2048 GELU, BF16 operands, FP32 accumulation and master weights",
+        "train_points": args.train_points, "epochs": epochs, "fit_s": t_fit, "final_loss": float(losses[-1]),
+        "check_points": int(check.shape[0]), "check_median_abs_d": float(np.median(d)),
+        "check_median_rel_d": float(np.median(d / exact_chk)),
+        "scan": {"rule": "error_bars", "keep_frac": 0.01, "margin_factor": 2.0, "tol": 0.05, "cells": r["n_cells"],
+                 "flagged_cells": r["n_flagged_cells"], "reevaluated": r["n_selected"],
+                 "ms_check": r["ms_check"], "ms_surrogate": r["ms_surrogate"], "ms_select": r["ms_select"],
+                 "ms_exact": r["ms_exact"], "ms_total": t_pre,
+                 "surrogate_evals_s": n / (r["ms_surrogate"] * 1e-3),
+                 "best_value": r["best_value"], "best_index": r["best_index"]},
+        "exact_scan": {"ms": ex["ms"], "evals_s": n / (ex["ms"] * 1e-3), "best_value": ex["best_value"],
+                       "best_index": ex["best_index"]},
+        "same_minimum": bool(r["best_index"] == ex["best_index"] and r["best_value"] == ex["best_value"]),
+        "gain": ex["ms"] / t_pre,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["bf16_tflops"], "kernel": "mlp_gemm_kernel (surrogate pass)",
+                     "flop_per_point": flop_point, "peak_source": "%s (bf16 burst)" % peak_src},
+    }
+
+
 # --------------------------------------------------------------------------- main arm
 def main():
     args = parse()
@@ -310,6 +363,13 @@ def main():
         prec = srw.PRECISIONS["fp16x3" if args.precision == "auto" else args.precision]
         peaks, peak_src = measured_peaks()
         print(json.dumps(grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)))
+        return 0
+
+    if args.surrogate_only:
+        wl = workloads.solar_set_workload()
+        with srw.Likelihood(wl, workloads.load_counts(WORKLOAD_DATA)) as lk0:
+            peaks, peak_src = measured_peaks()
+            print(json.dumps(surrogate_measurement(args, srw, workloads, lk0, peaks, peak_src)))
         return 0
 
     P = args.points
@@ -467,6 +527,8 @@ def main():
         line["clocks"] = clk
     if world == 1 and not args.no_grouped and prec != srw.SRW_FP32:
         line["grouped"] = grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)
+    if world == 1 and not args.no_surrogate and info["tensor_path"]:
+        line["surrogate"] = surrogate_measurement(args, srw, workloads, lk, peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         idx, vals, dt, fit = oracle_subprocess(P, args.cpu_sample, 3, n_fit)
         d = [abs(gpu_vals[i] - v) for i, v in zip(idx, vals)]
