@@ -72,6 +72,27 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def shard_theta_seed(rank):
+    """Each rank scans its own batch of points (weak scaling): seed of rank r's batch."""
+    return 3 + rank
+
+
+def max_over_ranks(total_ms, dist=None):
+    """The job's timed region: the slowest rank's (all ranks when dist is an
+    initialised torch.distributed module)."""
+    if dist is None:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, points, total_ms):
+    """Evaluations per second of all ranks together."""
+    return world * steps * points / (total_ms * 1e-3)
+
+
 def workload_config(P, precision, extra=None):
     cfg = {"workload": "solar_scan_%d" % P, "points": P, "n_t": 4096, "n_rec": 2048, "n_nodes": 8003,
            "n_bkg": 8, "precision": precision, "theta_box": "|eps|<=0.3, mu_hat in [0,3]", "l2": "flushed"}
@@ -373,7 +394,7 @@ def main():
         return 0
 
     P = args.points
-    wl = workloads.batched_scan_workload(P, theta_seed=3 + rank)
+    wl = workloads.batched_scan_workload(P, theta_seed=shard_theta_seed(rank))
     counts = workloads.load_counts(WORKLOAD_DATA)
     lk = srw.Likelihood(wl, counts)
     h = lk.handle
@@ -415,12 +436,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * P / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    value = whole_job_value(world, args.steps, P, total_ms)
     srw.srw_profile(h, False)
 
     # roofline of the fold kernel (useful flops 2 N_rec N_T per point)

@@ -405,6 +405,14 @@ srw_status srw_surrogate_get_standardization(srw_surrogate s, float* mean, float
 const char* srw_surrogate_last_error(srw_surrogate s);
 srw_status srw_surrogate_destroy(srw_surrogate s);
 
+/* Failure-detection diagnostic (the paper has no counterpart): launches one
+ * block on the current device whose thread waits, with the same bounded wait
+ * every kernel of the library uses, on an mbarrier that nothing arrives on.
+ * After about limit_us microseconds (1 .. 1e6) the wait gives up, the block
+ * records a timeout and returns; the call then reports SRW_ETIMEOUT (SRW_OK
+ * would mean the wait did not expire).  The context remains usable. */
+srw_status srw_diag_wait_timeout(unsigned limit_us);
+
 const char* srw_last_error(srw_handle h);
 const char* srw_status_string(srw_status s);
 srw_status srw_destroy(srw_handle h);

@@ -31,7 +31,8 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_group_last_error", "srw_group_destroy", "srw_surrogate_create", "srw_surrogate_set_weights",
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
-           "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization")
+           "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
+           "srw_diag_wait_timeout")
 
 
 class SrwError(RuntimeError):
@@ -139,6 +140,7 @@ def lib():
                                                ctypes.POINTER(ctypes.c_float)]
         L.srw_surrogate_sobol.argtypes = [vp, ctypes.c_longlong, ip, vp]
         L.srw_surrogate_get_standardization.argtypes = [vp, vp, vp]
+        L.srw_diag_wait_timeout.argtypes = [ctypes.c_uint]
         L.srw_surrogate_last_error.argtypes = [vp]
         L.srw_surrogate_last_error.restype = ctypes.c_char_p
         L.srw_surrogate_destroy.argtypes = [vp]

@@ -140,3 +140,18 @@ def test_device_pointers_on_torch_stream(srw):
     # far grid points: bounded by the rounding of the FP32 fold (see test_gpu_parity)
     bound = 1e-4 + 2 * 2.0 ** -22 * np.abs(mu - counts).sum(axis=1)
     assert np.all(np.abs(got - want) <= bound)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(srw):
+    # a wait on an mbarrier that nothing arrives on gives up after its limit
+    import time
+    t0 = time.perf_counter()
+    st = srw.lib().srw_diag_wait_timeout(2000)  # 2 ms
+    dt = time.perf_counter() - t0
+    assert st == 6  # SRW_ETIMEOUT
+    assert dt < 5.0
+    # the context is still usable: a normal evaluation afterwards
+    wl = workloads.be7_line_workload()
+    with srw.Likelihood(wl, workloads.load_counts(wl["name"])) as lk:
+        v = lk.loglik(np.zeros((2, 5), np.float32), srw.SRW_BF16X3)
+    assert np.all(np.isfinite(v))
