@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--surrogate-only", action="store_true", help="only the learned-surrogate measurement")
     ap.add_argument("--train-points", type=int, default=1_000_000, help="exact-path spectra the surrogate trains on")
     ap.add_argument("--scan-points", type=int, default=100_000_000, help="Sobol points of the pre-screened scan")
+    ap.add_argument("--epochs", type=int, default=40, help="surrogate training epochs")
     ap.add_argument("--groups", type=int, default=64, help="configurations of the grouped workload")
     ap.add_argument("--group-scale", type=float, default=1.0,
                     help="size factor of the grouped workload (profiling captures of a smaller case)")
@@ -318,7 +319,7 @@ def surrogate_measurement(args, srw, workloads, lk, peaks, peak_src):
 
     sg = srw.Surrogate(lk, init_weights(2048, seed=5), BOX_CENTRE, BOX_HALF)
     theta = workloads.theta_box(args.train_points, 5)
-    epochs = 40
+    epochs = args.epochs
     t0 = time.perf_counter()
     losses = sg.fit(theta, epochs=epochs, batch=4096, lr=2e-3, lr_final=2e-5)
     t_fit = time.perf_counter() - t0
