@@ -166,6 +166,21 @@ srw_status srw_loglik(srw_handle h, const float* theta, int P, double* out, int 
  * CUDA graph per call signature, like srw_loglik. */
 srw_status srw_loglik_points(srw_handle h, const float* theta, int P, double* out, int where, void* stream);
 
+/* Exact rank-8 evaluation of the same -2 ln L (the paper's pipeline has no
+ * counterpart; it follows from its equations): the recoil spectrum is linear
+ * in the eight coupling monomials c(theta) (Sec. II, eqs. g_tilde, xs_total),
+ * so the fold of eq. matrix_reweight is
+ *   mu(theta) = R W_ref + b + M (c(theta) - c_ref),  M = R shat^T  [n_rec][8],
+ * with M computed once in FP64 at srw_create.  Per point: eight coefficients,
+ * eight FMAs and one Poisson deviance per reconstructed bin (FP32), summed in
+ * double-float; no fold over the true bins.  grad (P x 5 float64, may be NULL)
+ * receives d(-2 ln L)/d theta from the same linearity:
+ *   2 sum_b (d c_b / d theta_k) sum_j M_jb (1 - n_j / mu_j).
+ * Values agree with the batched paths to rounding; `where`/`stream` as in
+ * srw_loglik; SRW_EDOMAIN (host calls) when a value is +inf. */
+srw_status srw_loglik_linear(srw_handle h, const float* theta, int P, double* out, double* grad, int where,
+                             void* stream);
+
 /* Folded signal spectra for P points with the batched fold:
  *   out[p * n_rec + j] = sum_i R_ji W_i(theta_p)   (P x n_rec float32)
  * in the requested precision (eq. matrix_reweight for a batch of points; no

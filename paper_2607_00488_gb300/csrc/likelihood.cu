@@ -293,7 +293,9 @@ cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s) {
   const int thr = 256;
   data_ref_kernel<<<(h->n_rec + thr - 1) / thr, thr, 0, s>>>(h->d_n64, h->d_b64, h->d_muref64, h->d_mask, h->n_rec,
                                                              h->d_bref64, h->d_nbm, h->d_nb2);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && h->d_lin) e = launch_linear_consts(h, s);
+  return e;
 }
 
 // out[p][j] += mu_ref[j]: folded spectra of the batched path from deviations.

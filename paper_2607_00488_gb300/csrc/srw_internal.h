@@ -150,6 +150,8 @@ struct srw_ctx {
   float* d_rinv = nullptr;         // [n_rec] inverse row scales of the FP16 split
   float wmax[8] = {};              // max_i |shat_b,i|
   float* d_wscale = nullptr;       // [P] per-point scales of the FP16 split (batched scratch)
+  double* d_linM = nullptr;        // [n_rec][8] M = R shat^T (FP64) of the rank-8 evaluator
+  float4* d_lin = nullptr;         // [3 n_rec] per-bin constants of the rank-8 evaluator
   int wscale_cap = 0;
 
   // data
@@ -234,6 +236,11 @@ FoldConfig tc_config(int i);
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
                            double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr);
 cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s);
+// linear.cu: exact rank-8 evaluation mu = mu_ref + b + M (c(theta) - c_ref).
+cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s);
+cudaError_t launch_linear_consts(srw_ctx* h, cudaStream_t s);
+cudaError_t launch_linear_loglik(const srw_ctx* h, const float* theta, int P, double* out, double* grad,
+                                 cudaStream_t s);
 // Per-point power-of-two scales of the FP16 split for a grouped launch.
 cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
                                 cudaStream_t s);

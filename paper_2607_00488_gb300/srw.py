@@ -32,7 +32,7 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
            "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
-           "srw_diag_wait_timeout")
+           "srw_diag_wait_timeout", "srw_loglik_linear")
 
 
 class SrwError(RuntimeError):
@@ -141,6 +141,7 @@ def lib():
         L.srw_surrogate_sobol.argtypes = [vp, ctypes.c_longlong, ip, vp]
         L.srw_surrogate_get_standardization.argtypes = [vp, vp, vp]
         L.srw_diag_wait_timeout.argtypes = [ctypes.c_uint]
+        L.srw_loglik_linear.argtypes = [vp, vp, ip, vp, vp, ip, vp]
         L.srw_surrogate_last_error.argtypes = [vp]
         L.srw_surrogate_last_error.restype = ctypes.c_char_p
         L.srw_surrogate_destroy.argtypes = [vp]
@@ -262,6 +263,27 @@ def srw_loglik(h, theta, precision=SRW_FP32, out=None, stream=None):
 def srw_loglik_points(h, theta, out=None, stream=None):
     """The plain single-point path applied to each point in turn."""
     return _loglik(lib().srw_loglik_points, h, theta, None, out, stream, extra_prec=False)
+
+
+def srw_loglik_linear(h, theta, out=None, grad=False, grad_out=None, stream=None):
+    """Exact rank-8 evaluation: -2 ln L for P points (and, with grad=True, the
+    gradient [P, 5]).  Host theta -> numpy results; CUDA tensors -> written into
+    out (and grad_out)."""
+    if _is_device(theta):
+        P = theta.numel() // 5
+        gp = ctypes.c_void_p(grad_out.data_ptr()) if grad_out is not None else None
+        _check(lib().srw_loglik_linear(h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()), gp,
+                                       SRW_DEVICE, _stream(stream)), h)
+        return (out, grad_out) if grad_out is not None else out
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
+    P = th.shape[0]
+    res = np.empty(P, dtype=np.float64)
+    g = np.empty((P, 5), dtype=np.float64) if grad else None
+    st = lib().srw_loglik_linear(h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p),
+                                 g.ctypes.data_as(ctypes.c_void_p) if grad else None, SRW_HOST, None)
+    if st != SRW_EDOMAIN:
+        _check(st, h)
+    return (res, g) if grad else res
 
 
 def srw_spectrum_batch(h, theta, precision=SRW_FP32, out=None, stream=None):
@@ -505,6 +527,9 @@ class Likelihood:
 
     def spectrum_batch(self, theta, precision=SRW_FP32, out=None, stream=None):
         return srw_spectrum_batch(self.handle, theta, precision, out, stream)
+
+    def loglik_linear(self, theta, out=None, grad=False, grad_out=None, stream=None):
+        return srw_loglik_linear(self.handle, theta, out, grad, grad_out, stream)
 
     def loglik_points(self, theta, out=None, stream=None):
         return srw_loglik_points(self.handle, theta, out, stream)

@@ -276,3 +276,66 @@ def test_full_scan_sampled(srw, solar, prec, tol):
         else:
             b = _budget(solar, th[k], solar.lk.spectrum_batch(th[k:k + 1], p)[0])
             assert abs(got[k] - want) <= tol + 2.0 * b
+
+
+# ---------------------------------------------------------------- exact rank-8 evaluator
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_linear_evaluator_matches_oracle(srw, name, request):
+    # mu = mu_ref + b + M (c - c_ref) with M in FP32: per-bin errors of 2^-24
+    # relative of mu_ref + b (carried as n - mu_ref - b and n + mu_ref + b) and of
+    # sum_b |M_jb dc_b|; fit region: the FP32 bar; everywhere: |d| <= tol + 2 B
+    # with B = 2 sum_j |1 - n_j / mu_j| (1.2e-7 mu_j + 1.2e-7 sum_b |M_jb dc_b|).
+    c = request.getfixturevalue(name)
+    wl = c.wl
+    fit = np.concatenate([np.zeros((1, 5), np.float32), near_sm(7, 31)])
+    box = workloads.theta_box(6, 32)
+    th = np.concatenate([fit, box])
+    got = c.lk.loglik_linear(th)
+    B = O.coefficient_spectra(wl["sources"], wl["t_edges"], wl["t_min"], wl["sin2w"], wl["f_tau"])
+    s_sm, e_sm = c.ref.s_sm, c.ref.e_sm
+    shat = np.where(s_sm > 0, B * (e_sm / np.where(s_sm > 0, s_sm, 1.0)), 0.0)
+    M = np.asarray(wl["R"], np.float64) @ shat.T  # [n_rec, 8]
+    c0 = O.coupling_coefficients(np.zeros(5), wl["sin2w"])
+    for k, t in enumerate(th):
+        t64 = t.astype(np.float64)
+        want = c.ref.neg2lnl(t64)
+        if k < fit.shape[0]:
+            assert abs(got[k] - want) <= TOL_FP32_LL, (k, got[k] - want)
+        mu = c.ref.mu(t64)
+        dc = O.coupling_coefficients(t64, wl["sin2w"]) - c0
+        on = mu > 0
+        eps = 1.2e-7 * mu + 1.2e-7 * np.abs(M * dc).sum(axis=1)
+        budget = 2.0 * np.sum(np.abs(1.0 - c.counts[on] / mu[on]) * eps[on])
+        assert abs(got[k] - want) <= TOL_FP32_LL + 2.0 * budget, (k, got[k] - want, budget)
+
+
+def test_linear_evaluator_equals_the_folds(srw, solar):
+    # two FP32 evaluations of the same quantity, each checked against the
+    # oracle above; at 1e5 events each stays within ~2e-4 of it in the fit
+    # region (largest seen: 1.7e-4), so their difference stays within 4e-4
+    # there, and within a relative 1e-6 far from the data (per-bin errors
+    # ~1e-7 times the residual sums)
+    fit = near_sm(100, 33)
+    box = workloads.theta_box(300, 34)
+    for th, rel in ((fit, 0.0), (box, 1e-6)):
+        lin = solar.lk.loglik_linear(th)
+        simt = solar.lk.loglik(th, srw.SRW_FP32)
+        tol = 4e-4 + rel * np.abs(simt)
+        assert np.all(np.abs(lin - simt) <= tol), np.max(np.abs(lin - simt) / tol)
+
+
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_linear_gradient_matches_finite_differences(srw, name, request):
+    c = request.getfixturevalue(name)
+    th = np.concatenate([near_sm(2, 35), workloads.theta_box(2, 36)]).astype(np.float64)
+    _, grad = c.lk.loglik_linear(th.astype(np.float32), grad=True)
+    h = 1e-5
+    for k, t in enumerate(th):
+        t = t.astype(np.float32).astype(np.float64)  # the point the GPU evaluated
+        fd = np.zeros(5)
+        for a in range(5):
+            e = np.zeros(5)
+            e[a] = h
+            fd[a] = (c.ref.neg2lnl(t + e) - c.ref.neg2lnl(t - e)) / (2 * h)
+        scale = np.max(np.abs(fd)) + 1.0
+        np.testing.assert_allclose(grad[k], fd, rtol=2e-3, atol=2e-4 * scale)
