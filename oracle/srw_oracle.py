@@ -347,3 +347,30 @@ class OracleModel:
 
     def neg2lnl_batch(self, thetas):
         return np.array([self.neg2lnl(t) for t in np.asarray(thetas, dtype=np.float64)])
+
+
+# ---------------------------------------------------------------------------
+# Profiled signal normalisation (a nuisance parameter of the fit, Sec. IV.B)
+# ---------------------------------------------------------------------------
+def profiled_neg2lnl(mu_sig, bkg, counts, sigma_alpha=0.0, mask=None):
+    """min over alpha >= 0 of -2 ln L(alpha mu_sig + bkg) + ((alpha - 1)/sigma)^2
+    (the pull term only when sigma_alpha > 0): the signal rate scaled by a free
+    or Gaussian-constrained normalisation.  The minimum is found with a bounded
+    scalar minimiser in float64 and returned with alpha-hat."""
+    from scipy.optimize import minimize_scalar
+    mu_sig = np.asarray(mu_sig, dtype=np.float64)
+    bkg = np.asarray(bkg, dtype=np.float64)
+
+    def f(a):
+        v = neg2lnl(a * mu_sig + bkg, counts, mask)
+        if sigma_alpha > 0.0:
+            v += ((a - 1.0) / sigma_alpha) ** 2
+        return v
+
+    # bracket: the objective is convex in alpha; search [0, a_hi]
+    a_hi = 2.0
+    while f(2.0 * a_hi) < f(a_hi) and a_hi < 1e6:
+        a_hi *= 2.0
+    r = minimize_scalar(f, bounds=(0.0, 2.0 * a_hi), method="bounded", options={"xatol": 1e-12, "maxiter": 500})
+    a = float(r.x)
+    return f(a), a
