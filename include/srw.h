@@ -181,6 +181,17 @@ srw_status srw_loglik_points(srw_handle h, const float* theta, int P, double* ou
 srw_status srw_loglik_linear(srw_handle h, const float* theta, int P, double* out, double* grad, int where,
                              void* stream);
 
+/* -2 ln L with the overall signal rate profiled (a nuisance of the fit, Sec.
+ * IV.B): per point
+ *   min over alpha >= 0 of  -2 ln L(mu = alpha mu_sig(theta) + b)  [+ ((alpha - 1)/sigma_alpha)^2]
+ * (the pull term only when sigma_alpha > 0; sigma_alpha = 0 leaves alpha
+ * free), mu_sig from the rank-8 form of srw_loglik_linear.  Eight Newton steps
+ * on the convex objective from alpha = 1, then the value at alpha-hat.
+ * alpha (P float64, may be NULL) receives alpha-hat.  `where`/`stream` as in
+ * srw_loglik. */
+srw_status srw_loglik_profiled(srw_handle h, const float* theta, int P, double sigma_alpha, double* out,
+                               double* alpha, int where, void* stream);
+
 /* Folded signal spectra for P points with the batched fold:
  *   out[p * n_rec + j] = sum_i R_ji W_i(theta_p)   (P x n_rec float32)
  * in the requested precision (eq. matrix_reweight for a batch of points; no

@@ -61,10 +61,12 @@ __global__ void linear_m_kernel(const float* __restrict__ R, int ld, int n_t, co
   }
 }
 
-// Per-bin constants: {M_j0..3}, {M_j4..7}, {n - mu_ref - b, n + mu_ref + b, n (or -1: masked), 0}.
+// Per-bin constants: {M_j0..3}, {M_j4..7}, {n - mu_ref - b, n + mu_ref + b, n (or -1: masked), 0},
+// and for the profiled evaluation {mu_ref, b, n (or -1), 0}.
 __global__ void linear_consts_kernel(const double* __restrict__ M, const double* __restrict__ n64,
-                                     const double* __restrict__ bref64, const unsigned char* __restrict__ mask,
-                                     int n_rec, float4* __restrict__ out) {
+                                     const double* __restrict__ bref64, const double* __restrict__ muref,
+                                     const unsigned char* __restrict__ mask, int n_rec, float4* __restrict__ out,
+                                     float4* __restrict__ outp) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_rec) return;
   const double* m = M + (size_t)j * kNB;
@@ -73,6 +75,7 @@ __global__ void linear_consts_kernel(const double* __restrict__ M, const double*
   out[3 * j] = make_float4((float)m[0], (float)m[1], (float)m[2], (float)m[3]);
   out[3 * j + 1] = make_float4((float)m[4], (float)m[5], (float)m[6], (float)m[7]);
   out[3 * j + 2] = make_float4((float)(n - base), (float)(n + base), on ? (float)n : -1.f, 0.f);
+  outp[j] = make_float4((float)muref[j], (float)(base - muref[j]), on ? (float)n : -1.f, 0.f);
 }
 
 struct Couplings {
@@ -194,7 +197,118 @@ linear_loglik_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefR
   }
 }
 
+constexpr int kNewton = 8;  // Newton steps for the normalisation (quadratic convergence from alpha = 1)
+
+// Profiled evaluation: min over alpha >= 0 of -2 ln L(alpha mu_sig + b) plus
+// ((alpha - 1)/sigma)^2 when sigma > 0, with mu_sig = mu_ref + M (c - c_ref).
+// Newton on the convex objective, g = 2 sum s (1 - n/mu) + 2 (alpha - 1)/sigma^2,
+// h = 2 sum n s^2 / mu^2 + 2 / sigma^2, each step one pass over the bins
+// (mu_sig recomputed from the eight coefficients); then the deviance at alpha.
+__global__ void __launch_bounds__(kLinThreads)
+linear_profiled_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef cref,
+                       const float4* __restrict__ consts, const float4* __restrict__ constp, int n_rec,
+                       float inv_var, const double* __restrict__ c_data, double* __restrict__ out,
+                       double* __restrict__ alpha_out, unsigned* __restrict__ status) {
+  __shared__ float4 sc[3 * kLinChunk];
+  const int quarter = threadIdx.x & 3;
+  const int p = blockIdx.x * (kLinThreads / 4) + (threadIdx.x >> 2);
+  const bool on = p < P;
+  float c[kNB] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  Couplings g{0.f, 0.f, 0.f, 0.f, 0.f};
+  if (on) deviations(theta + (size_t)p * 5, sin2w, cref, c, g);
+  auto stage = [&](int j0, int cnt) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      sc[3 * k] = consts[3 * (size_t)(j0 + k)];
+      sc[3 * k + 1] = consts[3 * (size_t)(j0 + k) + 1];
+      sc[3 * k + 2] = constp[j0 + k];
+    }
+    __syncthreads();
+  };
+  auto signal = [&](int j) {
+    const float4 m0 = sc[3 * j], m1 = sc[3 * j + 1];
+    float dl = m0.x * c[0];
+    dl = fmaf(m0.y, c[1], dl);
+    dl = fmaf(m0.z, c[2], dl);
+    dl = fmaf(m0.w, c[3], dl);
+    dl = fmaf(m1.x, c[4], dl);
+    dl = fmaf(m1.y, c[5], dl);
+    dl = fmaf(m1.z, c[6], dl);
+    dl = fmaf(m1.w, c[7], dl);
+    return sc[3 * j + 2].x + dl;
+  };
+  float alpha = 1.f;
+  for (int it = 0; it < kNewton; ++it) {
+    float G = 0.f, H = 0.f;
+    for (int j0 = 0; j0 < n_rec; j0 += kLinChunk) {
+      const int cnt = min(kLinChunk, n_rec - j0);
+      stage(j0, cnt);
+      for (int j = quarter; j < cnt; j += 4) {
+        const float4 q = sc[3 * j + 2];
+        const float s = signal(j);
+        const float mu = fmaf(alpha, s, q.y);
+        const bool live = q.z >= 0.f && mu > 0.f;
+        const float r = live ? __fdividef(q.z, mu) : 0.f;  // n / mu
+        G += q.z >= 0.f ? s * (1.f - r) : 0.f;
+        H += live ? r * s * s / mu : 0.f;
+      }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      G += __shfl_xor_sync(0xffffffffu, G, o);
+      H += __shfl_xor_sync(0xffffffffu, H, o);
+    }
+    const float gg = 2.f * G + 2.f * (alpha - 1.f) * inv_var, hh = 2.f * H + 2.f * inv_var;
+    float next = hh > 0.f ? alpha - gg / hh : (gg > 0.f ? 0.f : alpha);
+    alpha = fmaxf(next, 0.f);
+  }
+  dfloat acc = {0.f, 0.f};
+  bool infinite = false;
+  for (int j0 = 0; j0 < n_rec; j0 += kLinChunk) {
+    const int cnt = min(kLinChunk, n_rec - j0);
+    stage(j0, cnt);
+    float ts = 0.f;
+    int n_acc = 0;
+    for (int j = quarter; j < cnt; j += 4) {
+      const float4 q = sc[3 * j + 2];
+      const float mu = fmaf(alpha, signal(j), q.y);
+      const float t = deviance_ds(q.z - mu, q.z + mu, q.z);
+      ts += q.z >= 0.f ? t : 0.f;
+      if (++n_acc == 16) {
+        if (isinf(ts)) infinite = true;
+        else acc = df_add(acc, ts);
+        ts = 0.f;
+        n_acc = 0;
+      }
+    }
+    if (isinf(ts)) infinite = true;
+    else acc = df_add(acc, ts);
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    acc = df_add(acc, df_shfl_xor(acc, o));
+    infinite = __shfl_xor_sync(0xffffffffu, (int)infinite, o) || infinite;
+  }
+  if (!on || quarter != 0) return;
+  const double pull = (double)inv_var * ((double)alpha - 1.0) * ((double)alpha - 1.0);
+  const double v = infinite ? __longlong_as_double(0x7ff0000000000000LL)
+                            : 2.0 * ((double)acc.hi + (double)acc.lo) + *c_data + pull;
+  if (infinite) atomicOr(status, kStatusDomain);
+  out[p] = v;
+  if (alpha_out) alpha_out[p] = alpha;
+}
+
 }  // namespace
+
+cudaError_t launch_linear_profiled(const srw_ctx* h, const float* theta, int P, double sigma_alpha, double* out,
+                                   double* alpha, cudaStream_t s) {
+  const int grid = (P + kLinThreads / 4 - 1) / (kLinThreads / 4);
+  const float inv_var = sigma_alpha > 0.0 ? (float)(1.0 / (sigma_alpha * sigma_alpha)) : 0.f;
+  linear_profiled_kernel<<<grid, kLinThreads, 0, s>>>(theta, P, df_from_double(h->sin2w), h->cref, h->d_lin,
+                                                       h->d_linp, h->n_rec, inv_var, h->d_cdata, out, alpha,
+                                                       h->d_status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s) {
   linear_m_kernel<<<h->n_rec, 256, 0, s>>>(h->d_R, h->ld_r, h->n_t, h->d_basis, h->d_ssm64, h->d_esm64, h->d_linM);
@@ -202,8 +316,8 @@ cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s) {
 }
 
 cudaError_t launch_linear_consts(srw_ctx* h, cudaStream_t s) {
-  linear_consts_kernel<<<(h->n_rec + 255) / 256, 256, 0, s>>>(h->d_linM, h->d_n64, h->d_bref64, h->d_mask, h->n_rec,
-                                                             h->d_lin);
+  linear_consts_kernel<<<(h->n_rec + 255) / 256, 256, 0, s>>>(h->d_linM, h->d_n64, h->d_bref64, h->d_muref64, h->d_mask,
+                                                             h->n_rec, h->d_lin, h->d_linp);
   return cudaGetLastError();
 }
 

@@ -127,7 +127,7 @@ static void release(srw_ctx* h) {
   tc_release(h);
   dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_shat_lo); dfree(h->d_shat_k8); dfree(h->d_node64); dfree(h->d_bin_count); dfree(h->d_bin_f);
   dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis); dfree(h->d_ssm64); dfree(h->d_esm64);
-  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale); dfree(h->d_linM); dfree(h->d_lin);
+  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
   dfree(h->d_status); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
@@ -491,6 +491,7 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
   CREATE_CUDA(launch_spectrum_point(h, h->d_theta0, nullptr, nullptr, h->d_ssm32, s), "SM spectrum kernel");
   CREATE_CUDA(dalloc(h, &h->d_linM, (size_t)n_rec * kNB), "alloc rank-8 matrix");
   CREATE_CUDA(dalloc(h, &h->d_lin, 3 * (size_t)n_rec), "alloc rank-8 constants");
+  CREATE_CUDA(dalloc(h, &h->d_linp, (size_t)n_rec), "alloc rank-8 constants");
   CREATE_CUDA(launch_linear_m(h, s), "rank-8 matrix");
   set_reference_coefs(h);  // reference point: the SM (theta = 0)
   CREATE_CUDA(launch_reference_fold(h, s), "reference fold");
@@ -716,6 +717,52 @@ srw_status srw_loglik_linear(srw_handle h, const float* theta, int P, double* ou
     if (grad) {
       SRW_CUDA(h, cudaMemcpyAsync(grad, d_g, sizeof(double) * 5 * (size_t)P, cudaMemcpyDeviceToHost, s), "download");
       SRW_CUDA(h, cudaFreeAsync(d_g, s), "free gradient");
+    }
+    bool domain = false;
+    srw_status st = check_status_word(h, s, &domain);
+    if (st != SRW_OK) return st;
+    if (domain) return fail(h, SRW_EDOMAIN, "expected count <= 0 in a bin with data: value is +inf");
+  } else if (!stream) {
+    SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+  }
+  return SRW_OK;
+}
+
+srw_status srw_loglik_profiled(srw_handle h, const float* theta, int P, double sigma_alpha, double* out,
+                               double* alpha, int where, void* stream) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
+  if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
+  if (!(sigma_alpha >= 0.0) || !std::isfinite(sigma_alpha)) return fail(h, SRW_EINVAL, "sigma_alpha must be >= 0");
+  if (!h->has_data) return fail(h, SRW_ENODATA, "call srw_set_data first");
+  if (where != SRW_HOST && where != SRW_DEVICE) return fail(h, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
+  cudaStream_t s = pick_stream(h, stream);
+  const float* th = theta;
+  double *o = out, *a = alpha, *d_a = nullptr;
+  if (where == SRW_HOST) {
+    for (size_t q = 0; q < (size_t)P * 5; ++q)
+      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    srw_status st = ensure_staging(h, P);
+    if (st != SRW_OK) return st;
+    SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
+             "theta upload");
+    th = h->d_theta;
+    o = h->d_out;
+    if (alpha) {
+      SRW_CUDA(h, cudaMallocAsync(&d_a, sizeof(double) * (size_t)P, s), "alloc alpha");
+      a = d_a;
+    }
+  }
+  cudaError_t e = launch_linear_profiled(h, th, P, sigma_alpha, o, a, s);
+  if (e != cudaSuccess) {
+    if (d_a) cudaFreeAsync(d_a, s);
+    return cuda_fail(h, e, "profiled evaluation");
+  }
+  if (where == SRW_HOST) {
+    SRW_CUDA(h, cudaMemcpyAsync(out, o, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, s), "download");
+    if (alpha) {
+      SRW_CUDA(h, cudaMemcpyAsync(alpha, d_a, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, s), "download");
+      SRW_CUDA(h, cudaFreeAsync(d_a, s), "free alpha");
     }
     bool domain = false;
     srw_status st = check_status_word(h, s, &domain);

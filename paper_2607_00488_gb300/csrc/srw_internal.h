@@ -152,6 +152,7 @@ struct srw_ctx {
   float* d_wscale = nullptr;       // [P] per-point scales of the FP16 split (batched scratch)
   double* d_linM = nullptr;        // [n_rec][8] M = R shat^T (FP64) of the rank-8 evaluator
   float4* d_lin = nullptr;         // [3 n_rec] per-bin constants of the rank-8 evaluator
+  float4* d_linp = nullptr;        // [n_rec] {mu_ref, b, n, 0} for the profiled evaluation
   int wscale_cap = 0;
 
   // data
@@ -241,6 +242,8 @@ cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s);
 cudaError_t launch_linear_consts(srw_ctx* h, cudaStream_t s);
 cudaError_t launch_linear_loglik(const srw_ctx* h, const float* theta, int P, double* out, double* grad,
                                  cudaStream_t s);
+cudaError_t launch_linear_profiled(const srw_ctx* h, const float* theta, int P, double sigma_alpha, double* out,
+                                   double* alpha, cudaStream_t s);
 // Per-point power-of-two scales of the FP16 split for a grouped launch.
 cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
                                 cudaStream_t s);

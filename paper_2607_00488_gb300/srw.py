@@ -32,7 +32,7 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
            "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
-           "srw_diag_wait_timeout", "srw_loglik_linear")
+           "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled")
 
 
 class SrwError(RuntimeError):
@@ -142,6 +142,7 @@ def lib():
         L.srw_surrogate_get_standardization.argtypes = [vp, vp, vp]
         L.srw_diag_wait_timeout.argtypes = [ctypes.c_uint]
         L.srw_loglik_linear.argtypes = [vp, vp, ip, vp, vp, ip, vp]
+        L.srw_loglik_profiled.argtypes = [vp, vp, ip, ctypes.c_double, vp, vp, ip, vp]
         L.srw_surrogate_last_error.argtypes = [vp]
         L.srw_surrogate_last_error.restype = ctypes.c_char_p
         L.srw_surrogate_destroy.argtypes = [vp]
@@ -284,6 +285,21 @@ def srw_loglik_linear(h, theta, out=None, grad=False, grad_out=None, stream=None
     if st != SRW_EDOMAIN:
         _check(st, h)
     return (res, g) if grad else res
+
+
+def srw_loglik_profiled(h, theta, sigma_alpha=0.0):
+    """-2 ln L with the signal normalisation profiled (host theta [P, 5]);
+    returns (values, alpha-hat)."""
+    th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
+    P = th.shape[0]
+    res = np.empty(P, dtype=np.float64)
+    a = np.empty(P, dtype=np.float64)
+    st = lib().srw_loglik_profiled(h, th.ctypes.data_as(ctypes.c_void_p), P, float(sigma_alpha),
+                                   res.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p), SRW_HOST,
+                                   None)
+    if st != SRW_EDOMAIN:
+        _check(st, h)
+    return res, a
 
 
 def srw_spectrum_batch(h, theta, precision=SRW_FP32, out=None, stream=None):
@@ -530,6 +546,9 @@ class Likelihood:
 
     def loglik_linear(self, theta, out=None, grad=False, grad_out=None, stream=None):
         return srw_loglik_linear(self.handle, theta, out, grad, grad_out, stream)
+
+    def loglik_profiled(self, theta, sigma_alpha=0.0):
+        return srw_loglik_profiled(self.handle, theta, sigma_alpha)
 
     def loglik_points(self, theta, out=None, stream=None):
         return srw_loglik_points(self.handle, theta, out, stream)

@@ -339,3 +339,29 @@ def test_linear_gradient_matches_finite_differences(srw, name, request):
             fd[a] = (c.ref.neg2lnl(t + e) - c.ref.neg2lnl(t - e)) / (2 * h)
         scale = np.max(np.abs(fd)) + 1.0
         np.testing.assert_allclose(grad[k], fd, rtol=2e-3, atol=2e-4 * scale)
+
+
+# ---------------------------------------------------------------- profiled signal normalisation
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_profiled_normalisation_matches_oracle(srw, name, request):
+    # same FP32 evaluation as the rank-8 evaluator at alpha-hat: the fit-region
+    # bar of two FP32 paths (4e-4) near the data, 1e-6 relative far from it;
+    # alpha-hat to 1e-4 (the objective is flat in alpha at its minimum)
+    c = request.getfixturevalue(name)
+    th = np.concatenate([near_sm(3, 37), workloads.theta_box(2, 38)])
+    for sigma in (0.0, 0.05):
+        got, alpha = c.lk.loglik_profiled(th, sigma)
+        for k, t in enumerate(th):
+            want, a_want = O.profiled_neg2lnl(c.ref.mu_sig(t.astype(np.float64)), c.ref.bkg_sum, c.counts, sigma)
+            assert abs(got[k] - want) <= 4e-4 + 1e-6 * abs(want), (sigma, k, got[k] - want)
+            assert abs(alpha[k] - a_want) <= 1e-4 * max(1.0, a_want), (sigma, k, alpha[k], a_want)
+
+
+def test_profiled_asimov_recovers_the_normalisation(srw, be7):
+    from oracle.mlp_oracle import data_constant
+    theta0 = np.array([0.02, -0.01, 0.0, 0.0, 0.3])
+    counts = 1.3 * be7.ref.mu_sig(theta0) + be7.ref.bkg_sum  # Asimov data, oracle expectation
+    with srw.Likelihood(be7.wl, counts) as lk:
+        v, a = lk.loglik_profiled(theta0[None, :].astype(np.float32))
+    assert a[0] == pytest.approx(1.3, rel=1e-5)
+    assert v[0] == pytest.approx(data_constant(counts), abs=1e-3)
