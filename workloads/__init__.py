@@ -27,3 +27,11 @@ from .solar import (  # noqa: F401
     load_counts,
     counts_path,
 )
+from .joint import (  # noqa: F401
+    solar_components,
+    solar_joint_workload,
+    joint_workload,
+    live_time,
+    mc_histogram,
+    scale_factor,
+)
