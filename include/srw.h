@@ -129,6 +129,53 @@ typedef struct {
 srw_status srw_create(const srw_binning* binning, const srw_source* sources, int n_sources,
                       const float* R, const srw_options* options, srw_handle* out);
 
+/* Per-component joint response (Sec. III.B-C, eqs. Rij, fNp_reweight,
+ * mu_total).  Component k (sources[k] of srw_create_joint) comes with the 2-D
+ * histogram N^(k) of a detector simulation of its SM events, from which
+ *   R^(k)_ij = (N^(k)_ij / M^(k)_j) / sum_{i'j'} (N^(k)_i'j' / M^(k)_j') * s^(k)
+ * (eq. Rij; i = true recoil bin, j = reconstructed bin), and its expected
+ * counts are
+ *   mu_j = M_j sum_k N_k sum_i R^(k)_ij S^(k)_i(theta) / S^(k)_i(SM) + background_j,
+ * which is eq. mu_total with eq. fNp_reweight when the rate of a component
+ * follows its integrated cross section over the recoil bins: the
+ * normalisation prefactor of eq. fNp_reweight then cancels against
+ * rate_k(theta) / rate_k(SM), and N_k = MT rate_k(SM).  Where S^(k)_i(SM) = 0
+ * the weight is 1.  All arrays are host memory, row-major [n_rec][n_t] like
+ * the conditional R of srw_create. */
+typedef struct {
+  const double* const* hist;  /* n_sources pointers to N^(k), n_rec x n_t, finite and >= 0; every
+                                 histogram must hold some events */
+  const double* const* mask;  /* NULL, or n_sources pointers (an entry may be NULL = all ones) to the
+                                 live-time corrections M^(k)_j, n_rec values, finite and > 0 */
+  const double* scale;        /* n_sources scale factors s^(k) > 0, or NULL (all 1) */
+  const double* live;         /* n_rec common live-time factors M_j >= 0 of eq. mu_total, or NULL (all 1) */
+  const double* events;       /* n_sources SM event numbers N_k > 0, or NULL: N_k = lambda F_k with
+                                 F_k = sum_i S^(k)_i(SM) and lambda such that the SM signal
+                                 sum_j mu_j - background_j equals options->exposure */
+} srw_joint_response;
+
+/* Create a likelihood context whose fold runs over the concatenated
+ * (component, true bin) axis: one contraction sum over c = (k, i) of
+ * R_cat[j][c] W_c(theta) with R_cat[j][(k,i)] = M_j N_k R^(k)_ij and
+ * W_(k,i) = S^(k)_i(theta) / S^(k)_i(SM) (eq. fNp_reweight for every
+ * component at once).  Only true bins where a component's histogram has
+ * events enter the axis; its length is the handle's n_t (srw_info) and
+ * srw_joint_layout maps it back.  Every entry point taking a handle works on
+ * the result; srw_spectrum stage 0 / 1 return the per-component spectra /
+ * weights on the concatenated axis, srw_get_basis the concatenated
+ * coefficient spectra.  options->e_true_sm must be NULL.  binning->n_t is the
+ * recoil binning of every component.
+ * Errors: SRW_EINVAL (bad sizes/values, an empty histogram, a concatenated
+ * axis above 49152 columns), SRW_ENOMEM, SRW_ECUDA. */
+srw_status srw_create_joint(const srw_binning* binning, const srw_source* sources, int n_sources,
+                            const srw_joint_response* response, const srw_options* options, srw_handle* out);
+
+/* Columns of the fold axis: *n_columns receives its length; source[c] and
+ * bin[c] (host arrays of *n_columns ints, each may be NULL) receive the
+ * component and true bin of column c.  For an srw_create handle the axis is
+ * the true bins themselves (source 0). */
+srw_status srw_joint_layout(srw_handle h, int* n_columns, int* source, int* bin);
+
 /* Attach binned data (eqs. mu_total, logL).  Host pointers:
  *   counts: n_rec observed counts n_j >= 0 (need not be integers);
  *   bkg:    n_bkg x n_rec background templates in expected counts (summed);

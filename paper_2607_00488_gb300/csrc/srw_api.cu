@@ -226,118 +226,24 @@ static srw_status run_graph(srw_ctx* h, int path, int precision, int P, const vo
   return SRW_OK;
 }
 
-}  // namespace srw
-
-using namespace srw;
-
-extern "C" {
-
-const char* srw_status_string(srw_status s) {
-  switch (s) {
-    case SRW_OK: return "ok";
-    case SRW_EINVAL: return "invalid argument";
-    case SRW_ENOMEM: return "out of memory";
-    case SRW_ECUDA: return "CUDA error";
-    case SRW_ENODATA: return "no data set";
-    case SRW_EDOMAIN: return "expected count <= 0 where data > 0";
-    case SRW_ETIMEOUT: return "device wait timed out";
-    case SRW_EUNSUPPORTED: return "unsupported device";
-  }
-  return "unknown status";
-}
-
-const char* srw_last_error(srw_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
-
-srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_sources, const float* R,
-                      const srw_options* opt, srw_handle* out) {
-  g_create_err.clear();
-  if (!out) return fail(nullptr, SRW_EINVAL, "out handle pointer is NULL");
-  *out = nullptr;
-  if (!bin || !sources || !R || !opt) return fail(nullptr, SRW_EINVAL, "NULL binning/sources/R/options");
-  if (bin->n_t < 1 || bin->n_rec < 1 || !bin->t_edges)
-    return fail(nullptr, SRW_EINVAL, "n_t and n_rec must be >= 1 and t_edges non-NULL");
-  if (bin->n_t > 49152) return fail(nullptr, SRW_EINVAL, "n_t above the supported maximum 49152");
-  if (n_sources < 1) return fail(nullptr, SRW_EINVAL, "need at least one source");
-  const int n_t = bin->n_t, n_rec = bin->n_rec;
-  if (!finite_all(bin->t_edges, (size_t)n_t + 1) || bin->t_edges[0] < 0.0)
-    return fail(nullptr, SRW_EINVAL, "t_edges must be finite and >= 0");
-  for (int i = 0; i < n_t; ++i)
-    if (!(bin->t_edges[i + 1] > bin->t_edges[i])) return fail(nullptr, SRW_EINVAL, "t_edges must ascend strictly");
-  double t_min = bin->t_min > 0.0 ? bin->t_min : 1e-3;
-  if (!std::isfinite(t_min)) return fail(nullptr, SRW_EINVAL, "t_min must be finite");
-  if (!(opt->exposure > 0.0) || !std::isfinite(opt->exposure))
-    return fail(nullptr, SRW_EINVAL, "exposure must be finite and > 0");
-  const double sin2w = opt->sin2w > 0.0 ? opt->sin2w : 0.23121;
-  const double f_tau = opt->f_tau >= 0.0 ? opt->f_tau : 0.5;
-  if (!(sin2w < 1.0) || !(f_tau <= 1.0)) return fail(nullptr, SRW_EINVAL, "sin2w must be < 1 and f_tau <= 1");
-  long long n_nodes = 0;
-  for (int k = 0; k < n_sources; ++k) {
-    const srw_source& s = sources[k];
-    if (s.n_nodes < 1 || !s.e || !s.w || !s.pee) return fail(nullptr, SRW_EINVAL, "source with no nodes or NULL arrays");
-    for (int n = 0; n < s.n_nodes; ++n) {
-      if (!(s.e[n] > 0.0) || !std::isfinite(s.e[n])) return fail(nullptr, SRW_EINVAL, "node energies must be > 0");
-      if (!(s.w[n] >= 0.0) || !std::isfinite(s.w[n])) return fail(nullptr, SRW_EINVAL, "node weights must be >= 0");
-      if (!(s.pee[n] >= 0.0 && s.pee[n] <= 1.0)) return fail(nullptr, SRW_EINVAL, "P_ee must lie in [0, 1]");
-    }
-    n_nodes += s.n_nodes;
-  }
-  if (n_nodes > (1 << 26)) return fail(nullptr, SRW_EINVAL, "too many nodes");
-  for (size_t q = 0; q < (size_t)n_rec * n_t; ++q)
-    if (!(R[q] >= 0.f) || !std::isfinite(R[q])) return fail(nullptr, SRW_EINVAL, "R must be finite and >= 0");
-  if (opt->e_true_sm) {
-    if (!finite_all(opt->e_true_sm, n_t)) return fail(nullptr, SRW_EINVAL, "e_true_sm must be finite");
-    for (int i = 0; i < n_t; ++i)
-      if (opt->e_true_sm[i] < 0.0) return fail(nullptr, SRW_EINVAL, "e_true_sm must be >= 0");
-  }
-
-  int dev = 0, ndev = 0;
-  cudaError_t ce = cudaGetDeviceCount(&ndev);
-  if (ce != cudaSuccess || ndev == 0) return fail(nullptr, SRW_ECUDA, "no CUDA device available");
-  if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "cudaGetDevice failed");
-  cudaDeviceProp prop;
-  if ((ce = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "device properties");
-  if (!(prop.major == 10 && prop.minor == 3))
-    return fail(nullptr, SRW_EUNSUPPORTED, "this build targets sm_103a (GB300); device is sm_" +
-                                               std::to_string(prop.major) + std::to_string(prop.minor));
-
-  srw_ctx* h = new (std::nothrow) srw_ctx();
-  if (!h) return fail(nullptr, SRW_ENOMEM, "host allocation");
-  h->device = dev;
-  h->sm_count = prop.multiProcessorCount;
-  h->cc_major = prop.major;
-  h->cc_minor = prop.minor;
-  h->n_t = n_t;
-  h->n_rec = n_rec;
-  h->n_nodes = (int)n_nodes;
-  h->midpoint = bin->midpoint ? 1 : 0;
-  h->k_pad = (n_t + 63) / 64 * 64;
-  h->ld_r = h->k_pad;
-  h->rec_pad = (n_rec + 255) / 256 * 256;
-  h->t_min = t_min;
-  h->sin2w = sin2w;
-  h->f_tau = f_tau;
-  h->exposure = opt->exposure;
-  h->has_esm_input = opt->e_true_sm ? 1 : 0;
-  h->kappa = (kPi * kAlpha * kAlpha / (kMe * kMe)) / (2.0 * kGF * kGF * kMe / kPi) * kMuUnit * kMuUnit;
-
-  auto bail = [&](srw_status s) {
-    std::string msg = h->err;
-    release(h);
-    delete h;
-    fail(nullptr, s, msg);
-    return s;
-  };
-#define CREATE_CUDA(call, what)                       \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, what)); \
-  } while (0)
-
-  CREATE_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking), "stream create");
-  cudaStream_t s = h->own_stream;
-
+// Node and bin tables of a set of sources (replaces any previous tables).
+// Every "does node n reach bin i" decision is made here in FP64 and handed to
+// the kernels as integers: k_n = number of bins that lie entirely below
+// T_max(E_n) (integrated mode) or whose centre lies below it (midpoint mode).
+// Bins i < k_n are complete, bin k_n is clipped at T_max (integrated mode; its
+// integrals are precomputed in FP64 per node), bins above get nothing.  Nodes
+// are sorted by T_max descending, so k_n does not increase with n and the
+// nodes reaching bin i are the prefix k_n >= i.
+static cudaError_t upload_tables(srw_ctx* h, const srw_binning* bin, const srw_source* sources, int n_sources,
+                                 cudaStream_t s) {
+  dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_node64);
+  dfree(h->d_bin_count); dfree(h->d_bin_f); dfree(h->d_bin_l); dfree(h->d_bin64);
+  const int n_t = bin->n_t;
+  const double t_min = h->t_min, f_tau = h->f_tau;
+  int N = 0;
+  for (int k = 0; k < n_sources; ++k) N += sources[k].n_nodes;
+  h->n_nodes = N;
   // ---- nodes: flavour weights in FP64, sorted by T_max descending
-  const int N = h->n_nodes;
   std::vector<double> E(N), w(N), pe(N), pm(N), pt(N), tmax(N);
   {
     int q = 0;
@@ -370,14 +276,7 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
     node64[3 * (size_t)N + q] = w[o] * pt[o];
     node64[4 * (size_t)N + q] = w[o];
   }
-
-  // ---- bins.  Every "does node n reach bin i" decision is made here in FP64
-  // and handed to the kernels as integers: k_n = number of bins that lie
-  // entirely below T_max(E_n) (integrated mode) or whose centre lies below it
-  // (midpoint mode).  Bins i < k_n are complete, bin k_n is clipped at T_max
-  // (integrated mode; its integrals are precomputed in FP64 per node), bins
-  // above get nothing.  Nodes are sorted by T_max descending, so k_n does not
-  // increase with n and the nodes reaching bin i are the prefix k_n >= i.
+  // ---- bins
   std::vector<float4> bin_f(n_t);
   std::vector<float> bin_l(n_t);
   std::vector<double> bin64(2 * (size_t)n_t);
@@ -434,61 +333,364 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
   for (int i = 0; i < n_t; ++i)
     if (!h->midpoint && !(bin->t_edges[i + 1] > std::max(bin->t_edges[i], t_min))) bin_count[i] = 0;
 
-  // ---- device tables
+  cudaError_t e;
+#define TAB(call) \
+  if ((e = (call)) != cudaSuccess) return e
+  TAB(dalloc(h, &h->d_node_a, N));
+  TAB(dalloc(h, &h->d_node_w, N));
+  TAB(dalloc(h, &h->d_node_c, N));
+  TAB(dalloc(h, &h->d_node_wlo, N));
+  TAB(dalloc(h, &h->d_node64, 5 * (size_t)N));
+  TAB(dalloc(h, &h->d_bin_count, n_t));
+  TAB(dalloc(h, &h->d_bin_f, n_t));
+  TAB(dalloc(h, &h->d_bin_l, n_t));
+  TAB(dalloc(h, &h->d_bin64, 2 * (size_t)n_t));
+  TAB(cudaMemcpyAsync(h->d_node_a, node_a.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_node_w, node_w.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_node_c, node_c.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_node_wlo, node_wlo.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_node64, node64.data(), sizeof(double) * node64.size(), cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_bin_count, bin_count.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_bin_f, bin_f.data(), sizeof(float4) * n_t, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_bin_l, bin_l.data(), sizeof(float) * n_t, cudaMemcpyHostToDevice, s));
+  TAB(cudaMemcpyAsync(h->d_bin64, bin64.data(), sizeof(double) * bin64.size(), cudaMemcpyHostToDevice, s));
+#undef TAB
+  return cudaStreamSynchronize(s);  // the host tables go out of scope
+}
+
+// Device arrays sized by the fold axis (h->n_t columns, padded to k_pad) and
+// the reconstructed bins.
+static cudaError_t alloc_axis(srw_ctx* h, cudaStream_t s) {
+  const int n_t = h->n_t, n_rec = h->n_rec;
+  h->k_pad = (n_t + 63) / 64 * 64;
+  h->ld_r = h->k_pad;
   const size_t ld = h->ld_r;
-  CREATE_CUDA(dalloc(h, &h->d_node_a, N), "alloc nodes");
-  CREATE_CUDA(dalloc(h, &h->d_node_w, N), "alloc nodes");
-  CREATE_CUDA(dalloc(h, &h->d_node_c, N), "alloc nodes");
-  CREATE_CUDA(dalloc(h, &h->d_node_wlo, N), "alloc nodes");
-  CREATE_CUDA(dalloc(h, &h->d_node64, 5 * (size_t)N), "alloc nodes");
-  CREATE_CUDA(dalloc(h, &h->d_bin_count, n_t), "alloc bins");
-  CREATE_CUDA(dalloc(h, &h->d_bin_f, n_t), "alloc bins");
-  CREATE_CUDA(dalloc(h, &h->d_bin_l, n_t), "alloc bins");
-  CREATE_CUDA(dalloc(h, &h->d_bin64, 2 * (size_t)n_t), "alloc bins");
-  CREATE_CUDA(dalloc(h, &h->d_basis, (size_t)kNB * n_t), "alloc basis");
-  CREATE_CUDA(dalloc(h, &h->d_ssm64, n_t), "alloc");
-  CREATE_CUDA(dalloc(h, &h->d_esm64, n_t), "alloc");
-  CREATE_CUDA(dalloc(h, &h->d_ssm32, n_t), "alloc");
-  CREATE_CUDA(dalloc(h, &h->d_esm32, h->k_pad), "alloc");
-  CREATE_CUDA(dalloc(h, &h->d_shat, (size_t)kNB * h->k_pad), "alloc shat");
-  CREATE_CUDA(dalloc(h, &h->d_shat_lo, (size_t)kNB * h->k_pad), "alloc shat");
-  CREATE_CUDA(dalloc(h, &h->d_R, (size_t)n_rec * ld), "alloc R");
-  CREATE_CUDA(dalloc(h, &h->d_W, h->k_pad), "alloc W");
-  CREATE_CUDA(dalloc(h, &h->d_S, n_t), "alloc S");
-  CREATE_CUDA(dalloc(h, &h->d_musig, n_rec), "alloc");
-  CREATE_CUDA(dalloc(h, &h->d_muref64, n_rec), "alloc reference fold");
-  CREATE_CUDA(dalloc(h, &h->d_mu, n_rec), "alloc");
+  cudaError_t e;
+#define AX(call) \
+  if ((e = (call)) != cudaSuccess) return e
+  AX(dalloc(h, &h->d_basis, (size_t)kNB * n_t));
+  AX(dalloc(h, &h->d_ssm64, n_t));
+  AX(dalloc(h, &h->d_esm64, n_t));
+  AX(dalloc(h, &h->d_ssm32, n_t));
+  AX(dalloc(h, &h->d_esm32, h->k_pad));
+  AX(dalloc(h, &h->d_shat, (size_t)kNB * h->k_pad));
+  AX(dalloc(h, &h->d_shat_lo, (size_t)kNB * h->k_pad));
+  AX(dalloc(h, &h->d_R, (size_t)n_rec * ld));
+  AX(dalloc(h, &h->d_W, h->k_pad));
+  AX(dalloc(h, &h->d_S, n_t));
+  AX(dalloc(h, &h->d_musig, n_rec));
+  AX(dalloc(h, &h->d_muref64, n_rec));
+  AX(dalloc(h, &h->d_mu, n_rec));
   h->part_cap = fold_point_grid(h);
-  CREATE_CUDA(dalloc(h, &h->d_part, h->part_cap), "alloc partials");
-  CREATE_CUDA(dalloc(h, &h->d_ticket, 1), "alloc ticket");
-  CREATE_CUDA(dalloc(h, &h->d_status, 1), "alloc status");
-  CREATE_CUDA(dalloc(h, &h->d_theta0, 8), "alloc");
-  CREATE_CUDA(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned), s), "memset");
-  CREATE_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "memset");
-  CREATE_CUDA(cudaMemsetAsync(h->d_theta0, 0, sizeof(float) * 8, s), "memset");
-  CREATE_CUDA(cudaMemsetAsync(h->d_W, 0, sizeof(float) * h->k_pad, s), "memset");
-  CREATE_CUDA(cudaMemsetAsync(h->d_esm32, 0, sizeof(float) * h->k_pad, s), "memset");
+  AX(dalloc(h, &h->d_part, h->part_cap));
+  AX(dalloc(h, &h->d_ticket, 1));
+  AX(dalloc(h, &h->d_status, 1));
+  AX(dalloc(h, &h->d_theta0, 8));
+  AX(cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned), s));
+  AX(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s));
+  AX(cudaMemsetAsync(h->d_theta0, 0, sizeof(float) * 8, s));
+  AX(cudaMemsetAsync(h->d_W, 0, sizeof(float) * h->k_pad, s));
+  AX(cudaMemsetAsync(h->d_esm32, 0, sizeof(float) * h->k_pad, s));
+  AX(cudaMemsetAsync(h->d_ssm32, 0, sizeof(float) * n_t, s));
+  AX(cudaMemsetAsync(h->d_R, 0, sizeof(float) * (size_t)n_rec * ld, s));
+#undef AX
+  return cudaSuccess;
+}
 
-  CREATE_CUDA(cudaMemcpyAsync(h->d_node_a, node_a.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_node_w, node_w.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_node_c, node_c.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_node_wlo, node_wlo.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_node64, node64.data(), sizeof(double) * node64.size(), cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_count, bin_count.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_f, bin_f.data(), sizeof(float4) * n_t, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_bin_l, bin_l.data(), sizeof(float) * n_t, cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemcpyAsync(h->d_bin64, bin64.data(), sizeof(double) * bin64.size(), cudaMemcpyHostToDevice, s), "upload");
-  CREATE_CUDA(cudaMemsetAsync(h->d_R, 0, sizeof(float) * (size_t)n_rec * ld, s), "memset R");
-  CREATE_CUDA(cudaMemcpy2DAsync(h->d_R, ld * sizeof(float), R, (size_t)n_t * sizeof(float), (size_t)n_t * sizeof(float),
-                                n_rec, cudaMemcpyHostToDevice, s), "upload R");
-  if (h->has_esm_input)
-    CREATE_CUDA(cudaMemcpyAsync(h->d_esm64, opt->e_true_sm, sizeof(double) * n_t, cudaMemcpyHostToDevice, s), "upload");
+// Joint response (eq. Rij) of every component on the concatenated axis:
+// per-component FP64 coefficient spectra, the live-time-corrected histogram
+// sums, the event numbers N_k, then R_cat, the concatenated coefficient
+// spectra and the weights' baseline E = 1 (W_c = S_c(theta) / S_SM,c).
+static srw_status build_joint(srw_ctx* h, const srw_binning* bin, const srw_source* sources, int n_src,
+                              const srw_joint_response* jr, cudaStream_t s) {
+  const int n_t = bin->n_t, n_rec = h->n_rec;
+  cudaError_t e;
+#define JC(call, what)                                        \
+  do {                                                        \
+    if ((e = (call)) != cudaSuccess) return cuda_fail(h, e, what); \
+  } while (0)
+  // ---- coefficient spectra of each component (G0, FP64)
+  std::vector<double> basis_all((size_t)n_src * kNB * n_t);
+  h->n_t = n_t;
+  JC(dalloc(h, &h->d_basis, (size_t)kNB * n_t), "alloc basis");
+  for (int k = 0; k < n_src; ++k) {
+    JC(upload_tables(h, bin, &sources[k], 1, s), "node tables");
+    JC(launch_basis_fp64(h, s), "basis kernel");
+    JC(cudaMemcpyAsync(basis_all.data() + (size_t)k * kNB * n_t, h->d_basis, sizeof(double) * kNB * n_t,
+                       cudaMemcpyDeviceToHost, s), "basis download");
+    JC(cudaStreamSynchronize(s), "basis sync");
+  }
+  dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_node64);
+  dfree(h->d_bin_count); dfree(h->d_bin_f); dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis);
+  int total_nodes = 0;
+  for (int k = 0; k < n_src; ++k) total_nodes += sources[k].n_nodes;
+  h->n_nodes = total_nodes;
+  h->device_bytes = 0;  // every persistent array so far was temporary
+  // SM spectra and their integrals F_k (FP64, host): c(SM) of the unshifted couplings
+  const double s2 = h->sin2w, gle = 0.5 + s2, gre = s2, glt = -0.5 + s2, grt = s2;
+  const double csm[kNB] = {gle * gle, gre * gre, -gle * gre, glt * glt, grt * grt, -glt * grt, 1.0, 0.0};
+  std::vector<double> F(n_src, 0.0);
+  for (int k = 0; k < n_src; ++k)
+    for (int i = 0; i < n_t; ++i) {
+      double v = 0.0;
+      for (int b = 0; b < kNB; ++b) v += csm[b] * basis_all[((size_t)k * kNB + b) * n_t + i];
+      F[k] += v;
+    }
 
+  // ---- histogram sums (FP64, device)
+  const size_t cells = (size_t)n_rec * n_t;
+  double *d_hist = nullptr, *d_mask = nullptr, *d_live = nullptr, *d_col = nullptr;
+  int* d_cols = nullptr;
+  auto free_tmp = [&]() {
+    dfree(d_hist); dfree(d_mask); dfree(d_live); dfree(d_col); dfree(d_cols);
+  };
+  auto jfail = [&](cudaError_t ce, const char* what) {
+    free_tmp();
+    return cuda_fail(h, ce, what);
+  };
+#define JT(call, what)                               \
+  do {                                               \
+    if ((e = (call)) != cudaSuccess) return jfail(e, what); \
+  } while (0)
+  JT(cudaMalloc(&d_hist, sizeof(double) * cells * n_src), "alloc histograms");
+  JT(cudaMalloc(&d_mask, sizeof(double) * (size_t)n_rec * n_src), "alloc masks");
+  JT(cudaMalloc(&d_live, sizeof(double) * n_rec), "alloc live time");
+  JT(cudaMalloc(&d_col, sizeof(double) * 2 * (size_t)n_t * n_src), "alloc column sums");
+  std::vector<double> ones(std::max(n_rec, 1), 1.0), live(n_rec, 1.0);
+  if (jr->live) std::copy(jr->live, jr->live + n_rec, live.begin());
+  JT(cudaMemcpyAsync(d_live, live.data(), sizeof(double) * n_rec, cudaMemcpyHostToDevice, s), "upload live time");
+  for (int k = 0; k < n_src; ++k) {
+    const double* m = (jr->mask && jr->mask[k]) ? jr->mask[k] : ones.data();
+    JT(cudaMemcpyAsync(d_hist + cells * k, jr->hist[k], sizeof(double) * cells, cudaMemcpyHostToDevice, s),
+       "upload histogram");
+    JT(cudaMemcpyAsync(d_mask + (size_t)n_rec * k, m, sizeof(double) * n_rec, cudaMemcpyHostToDevice, s),
+       "upload mask");
+    JT(launch_joint_colsums(d_hist + cells * k, d_mask + (size_t)n_rec * k, d_live, n_rec, n_t,
+                            d_col + 2 * (size_t)n_t * k, d_col + 2 * (size_t)n_t * k + n_t, s),
+       "histogram sums");
+  }
+  std::vector<double> col(2 * (size_t)n_t * n_src);
+  JT(cudaMemcpyAsync(col.data(), d_col, sizeof(double) * col.size(), cudaMemcpyDeviceToHost, s), "download sums");
+  JT(cudaStreamSynchronize(s), "sums sync");
+  std::vector<double> Z(n_src, 0.0), Y(n_src, 0.0), N(n_src, 0.0), scale(n_src, 1.0);
+  std::vector<std::vector<int>> cols(n_src);
+  int K = 0;
+  for (int k = 0; k < n_src; ++k) {
+    const double* cz = col.data() + 2 * (size_t)n_t * k;
+    const double* cy = cz + n_t;
+    for (int i = 0; i < n_t; ++i) {
+      Z[k] += cz[i];
+      Y[k] += cy[i];
+      if (cz[i] > 0.0) cols[k].push_back(i);
+    }
+    if (!(Z[k] > 0.0)) {
+      free_tmp();
+      return fail(h, SRW_EINVAL, "the histogram of component " + std::to_string(k) + " holds no events");
+    }
+    if (jr->scale) scale[k] = jr->scale[k];
+    K += (int)cols[k].size();
+  }
+  if (K > 49152) {
+    free_tmp();
+    return fail(h, SRW_EINVAL, "the concatenated (component, true bin) axis exceeds 49152 columns");
+  }
+  // N_k: given, or lambda F_k with the SM signal sum_j M_j sum_k N_k sum_i R^(k)_ij = exposure
+  double lambda = 0.0;
+  if (jr->events) {
+    for (int k = 0; k < n_src; ++k) N[k] = jr->events[k];
+  } else {
+    double per = 0.0;
+    for (int k = 0; k < n_src; ++k) per += F[k] * scale[k] * Y[k] / Z[k];
+    if (!(per > 0.0) || !std::isfinite(per)) {
+      free_tmp();
+      return fail(h, SRW_EINVAL, "the SM signal of the components folds to zero: cannot normalise the exposure");
+    }
+    lambda = h->exposure / per;
+    for (int k = 0; k < n_src; ++k) N[k] = lambda * F[k];
+  }
+  h->lambda = lambda;
+
+  // ---- the concatenated axis
+  h->n_t = K;
+  JT(alloc_axis(h, s), "alloc");
+  std::vector<int> all_cols;
+  all_cols.reserve(K);
+  h->col_src.clear();
+  h->col_bin.clear();
+  for (int k = 0; k < n_src; ++k)
+    for (int i : cols[k]) {
+      all_cols.push_back(i);
+      h->col_src.push_back(k);
+      h->col_bin.push_back(i);
+    }
+  JT(cudaMalloc(&d_cols, sizeof(int) * std::max(K, 1)), "alloc columns");
+  JT(cudaMemcpyAsync(d_cols, all_cols.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s), "upload columns");
+  int col0 = 0;
+  for (int k = 0; k < n_src; ++k) {
+    const int nk = (int)cols[k].size();
+    JT(launch_joint_gather(d_hist + cells * k, d_mask + (size_t)n_rec * k, d_live, n_rec, n_t, d_cols + col0, nk,
+                           N[k] * scale[k] / Z[k], h->d_R, h->ld_r, col0, s),
+       "joint response gather");
+    col0 += nk;
+  }
+  std::vector<double> basis_cat((size_t)kNB * K), esm(K, 1.0);
+  for (int c = 0; c < K; ++c) {
+    const int k = h->col_src[c], i = h->col_bin[c];
+    for (int b = 0; b < kNB; ++b) basis_cat[(size_t)b * K + c] = basis_all[((size_t)k * kNB + b) * n_t + i];
+  }
+  JT(cudaMemcpyAsync(h->d_basis, basis_cat.data(), sizeof(double) * basis_cat.size(), cudaMemcpyHostToDevice, s),
+     "upload basis");
+  JT(cudaMemcpyAsync(h->d_esm64, esm.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s), "upload baseline");
+  h->has_esm_input = 1;
+  JT(launch_build_shat(h, s), "shat kernels");
+  JT(cudaStreamSynchronize(s), "joint sync");
+  free_tmp();
+#undef JT
+#undef JC
+  return SRW_OK;
+}
+
+// Checks shared by srw_create and srw_create_joint.
+static srw_status validate_model(const srw_binning* bin, const srw_source* sources, int n_sources,
+                                 const srw_options* opt) {
+  if (bin->n_t < 1 || bin->n_rec < 1 || !bin->t_edges)
+    return fail(nullptr, SRW_EINVAL, "n_t and n_rec must be >= 1 and t_edges non-NULL");
+  if (bin->n_t > 49152) return fail(nullptr, SRW_EINVAL, "n_t above the supported maximum 49152");
+  if (n_sources < 1) return fail(nullptr, SRW_EINVAL, "need at least one source");
+  const int n_t = bin->n_t;
+  if (!finite_all(bin->t_edges, (size_t)n_t + 1) || bin->t_edges[0] < 0.0)
+    return fail(nullptr, SRW_EINVAL, "t_edges must be finite and >= 0");
+  for (int i = 0; i < n_t; ++i)
+    if (!(bin->t_edges[i + 1] > bin->t_edges[i])) return fail(nullptr, SRW_EINVAL, "t_edges must ascend strictly");
+  if (!std::isfinite(bin->t_min > 0.0 ? bin->t_min : 1e-3)) return fail(nullptr, SRW_EINVAL, "t_min must be finite");
+  if (!(opt->exposure > 0.0) || !std::isfinite(opt->exposure))
+    return fail(nullptr, SRW_EINVAL, "exposure must be finite and > 0");
+  const double sin2w = opt->sin2w > 0.0 ? opt->sin2w : 0.23121;
+  const double f_tau = opt->f_tau >= 0.0 ? opt->f_tau : 0.5;
+  if (!(sin2w < 1.0) || !(f_tau <= 1.0)) return fail(nullptr, SRW_EINVAL, "sin2w must be < 1 and f_tau <= 1");
+  long long n_nodes = 0;
+  for (int k = 0; k < n_sources; ++k) {
+    const srw_source& s = sources[k];
+    if (s.n_nodes < 1 || !s.e || !s.w || !s.pee) return fail(nullptr, SRW_EINVAL, "source with no nodes or NULL arrays");
+    for (int n = 0; n < s.n_nodes; ++n) {
+      if (!(s.e[n] > 0.0) || !std::isfinite(s.e[n])) return fail(nullptr, SRW_EINVAL, "node energies must be > 0");
+      if (!(s.w[n] >= 0.0) || !std::isfinite(s.w[n])) return fail(nullptr, SRW_EINVAL, "node weights must be >= 0");
+      if (!(s.pee[n] >= 0.0 && s.pee[n] <= 1.0)) return fail(nullptr, SRW_EINVAL, "P_ee must lie in [0, 1]");
+    }
+    n_nodes += s.n_nodes;
+  }
+  if (n_nodes > (1 << 26)) return fail(nullptr, SRW_EINVAL, "too many nodes");
+  return SRW_OK;
+}
+
+static srw_status validate_joint(const srw_binning* bin, int n_sources, const srw_joint_response* jr,
+                                 const srw_options* opt) {
+  if (!jr->hist) return fail(nullptr, SRW_EINVAL, "joint response without histograms");
+  if (opt->e_true_sm) return fail(nullptr, SRW_EINVAL, "e_true_sm is not used with a joint response: pass NULL");
+  const size_t cells = (size_t)bin->n_rec * bin->n_t;
+  for (int k = 0; k < n_sources; ++k) {
+    const double* hk = jr->hist[k];
+    if (!hk) return fail(nullptr, SRW_EINVAL, "NULL histogram");
+    for (size_t q = 0; q < cells; ++q)
+      if (!(hk[q] >= 0.0) || !std::isfinite(hk[q])) return fail(nullptr, SRW_EINVAL, "histograms must be finite and >= 0");
+    if (jr->mask && jr->mask[k])
+      for (int j = 0; j < bin->n_rec; ++j)
+        if (!(jr->mask[k][j] > 0.0) || !std::isfinite(jr->mask[k][j]))
+          return fail(nullptr, SRW_EINVAL, "live-time corrections must be finite and > 0");
+    if (jr->scale && (!(jr->scale[k] > 0.0) || !std::isfinite(jr->scale[k])))
+      return fail(nullptr, SRW_EINVAL, "scale factors must be finite and > 0");
+    if (jr->events && (!(jr->events[k] > 0.0) || !std::isfinite(jr->events[k])))
+      return fail(nullptr, SRW_EINVAL, "event numbers must be finite and > 0");
+  }
+  if (jr->live)
+    for (int j = 0; j < bin->n_rec; ++j)
+      if (!(jr->live[j] >= 0.0) || !std::isfinite(jr->live[j]))
+        return fail(nullptr, SRW_EINVAL, "live-time factors must be finite and >= 0");
+  return SRW_OK;
+}
+
+// srw_create (R != NULL, conditional response) and srw_create_joint (jr != NULL).
+static srw_status create_impl(const srw_binning* bin, const srw_source* sources, int n_sources, const float* R,
+                              const srw_joint_response* jr, const srw_options* opt, srw_handle* out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, SRW_EINVAL, "out handle pointer is NULL");
+  *out = nullptr;
+  if (!bin || !sources || (!R && !jr) || !opt) return fail(nullptr, SRW_EINVAL, "NULL binning/sources/response/options");
+  srw_status vs = validate_model(bin, sources, n_sources, opt);
+  if (vs != SRW_OK) return vs;
+  const int n_t = bin->n_t, n_rec = bin->n_rec;
+  if (R) {
+    for (size_t q = 0; q < (size_t)n_rec * n_t; ++q)
+      if (!(R[q] >= 0.f) || !std::isfinite(R[q])) return fail(nullptr, SRW_EINVAL, "R must be finite and >= 0");
+    if (opt->e_true_sm) {
+      if (!finite_all(opt->e_true_sm, n_t)) return fail(nullptr, SRW_EINVAL, "e_true_sm must be finite");
+      for (int i = 0; i < n_t; ++i)
+        if (opt->e_true_sm[i] < 0.0) return fail(nullptr, SRW_EINVAL, "e_true_sm must be >= 0");
+    }
+  } else if ((vs = validate_joint(bin, n_sources, jr, opt)) != SRW_OK) {
+    return vs;
+  }
+
+  int dev = 0, ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) return fail(nullptr, SRW_ECUDA, "no CUDA device available");
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "cudaGetDevice failed");
+  cudaDeviceProp prop;
+  if ((ce = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "device properties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, SRW_EUNSUPPORTED, "this build targets sm_103a (GB300); device is sm_" +
+                                               std::to_string(prop.major) + std::to_string(prop.minor));
+
+  srw_ctx* h = new (std::nothrow) srw_ctx();
+  if (!h) return fail(nullptr, SRW_ENOMEM, "host allocation");
+  h->device = dev;
+  h->sm_count = prop.multiProcessorCount;
+  h->cc_major = prop.major;
+  h->cc_minor = prop.minor;
+  h->n_t = n_t;
+  h->n_rec = n_rec;
+  h->midpoint = bin->midpoint ? 1 : 0;
+  h->rec_pad = (n_rec + 255) / 256 * 256;
+  h->t_min = bin->t_min > 0.0 ? bin->t_min : 1e-3;
+  h->sin2w = opt->sin2w > 0.0 ? opt->sin2w : 0.23121;
+  h->f_tau = opt->f_tau >= 0.0 ? opt->f_tau : 0.5;
+  h->exposure = opt->exposure;
+  h->joint = jr ? 1 : 0;
+  h->has_esm_input = (!jr && opt->e_true_sm) ? 1 : 0;
+  h->kappa = (kPi * kAlpha * kAlpha / (kMe * kMe)) / (2.0 * kGF * kGF * kMe / kPi) * kMuUnit * kMuUnit;
+
+  auto bail = [&](srw_status st) {
+    std::string msg = h->err;
+    release(h);
+    delete h;
+    fail(nullptr, st, msg);
+    return st;
+  };
+#define CREATE_CUDA(call, what)                       \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, what)); \
+  } while (0)
+
+  CREATE_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking), "stream create");
+  cudaStream_t s = h->own_stream;
   fold_point_init();
-  // ---- G0 coefficient spectra (FP64), S_SM, E_SM, shat; then S_SM of the FP32 kernel
-  CREATE_CUDA(launch_basis_fp64(h, s), "basis kernel");
-  CREATE_CUDA(launch_build_shat(h, s), "shat kernels");
-  CREATE_CUDA(launch_spectrum_point(h, h->d_theta0, nullptr, nullptr, h->d_ssm32, s), "SM spectrum kernel");
+
+  if (!jr) {
+    CREATE_CUDA(upload_tables(h, bin, sources, n_sources, s), "node tables");
+    CREATE_CUDA(alloc_axis(h, s), "alloc");
+    CREATE_CUDA(cudaMemcpy2DAsync(h->d_R, (size_t)h->ld_r * sizeof(float), R, (size_t)n_t * sizeof(float),
+                                  (size_t)n_t * sizeof(float), n_rec, cudaMemcpyHostToDevice, s), "upload R");
+    if (h->has_esm_input)
+      CREATE_CUDA(cudaMemcpyAsync(h->d_esm64, opt->e_true_sm, sizeof(double) * n_t, cudaMemcpyHostToDevice, s), "upload");
+    // ---- G0 coefficient spectra (FP64), S_SM, E_SM, shat; then S_SM of the FP32 kernel
+    CREATE_CUDA(launch_basis_fp64(h, s), "basis kernel");
+    CREATE_CUDA(launch_build_shat(h, s), "shat kernels");
+    CREATE_CUDA(launch_spectrum_point(h, h->d_theta0, nullptr, nullptr, h->d_ssm32, s), "SM spectrum kernel");
+  } else {
+    srw_status st = build_joint(h, bin, sources, n_sources, jr, s);
+    if (st != SRW_OK) return bail(st);
+  }
   CREATE_CUDA(dalloc(h, &h->d_linM, (size_t)n_rec * kNB), "alloc rank-8 matrix");
   CREATE_CUDA(dalloc(h, &h->d_lin, 3 * (size_t)n_rec), "alloc rank-8 constants");
   CREATE_CUDA(dalloc(h, &h->d_linp, (size_t)n_rec), "alloc rank-8 constants");
@@ -496,7 +698,7 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
   set_reference_coefs(h);  // reference point: the SM (theta = 0)
   CREATE_CUDA(launch_reference_fold(h, s), "reference fold");
   CREATE_CUDA(cudaStreamSynchronize(s), "create sync");
-  if (!h->has_esm_input && !(h->lambda > 0.0))
+  if (!jr && !h->has_esm_input && !(h->lambda > 0.0))
     return bail(fail(h, SRW_EINVAL, "the SM spectrum folded through R is zero: cannot normalise the exposure"));
 
   // ---- tensor-core path: BF16 hi/lo split of R and TMA descriptors
@@ -526,6 +728,59 @@ srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_s
   *out = h;
   return SRW_OK;
 #undef CREATE_CUDA
+}
+
+}  // namespace srw
+
+using namespace srw;
+
+extern "C" {
+
+const char* srw_status_string(srw_status s) {
+  switch (s) {
+    case SRW_OK: return "ok";
+    case SRW_EINVAL: return "invalid argument";
+    case SRW_ENOMEM: return "out of memory";
+    case SRW_ECUDA: return "CUDA error";
+    case SRW_ENODATA: return "no data set";
+    case SRW_EDOMAIN: return "expected count <= 0 where data > 0";
+    case SRW_ETIMEOUT: return "device wait timed out";
+    case SRW_EUNSUPPORTED: return "unsupported device";
+  }
+  return "unknown status";
+}
+
+const char* srw_last_error(srw_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+srw_status srw_create(const srw_binning* bin, const srw_source* sources, int n_sources, const float* R,
+                      const srw_options* opt, srw_handle* out) {
+  if (!R) {
+    g_create_err = "NULL R";
+    if (out) *out = nullptr;
+    return SRW_EINVAL;
+  }
+  return create_impl(bin, sources, n_sources, R, nullptr, opt, out);
+}
+
+srw_status srw_create_joint(const srw_binning* bin, const srw_source* sources, int n_sources,
+                            const srw_joint_response* response, const srw_options* opt, srw_handle* out) {
+  if (!response) {
+    g_create_err = "NULL joint response";
+    if (out) *out = nullptr;
+    return SRW_EINVAL;
+  }
+  return create_impl(bin, sources, n_sources, nullptr, response, opt, out);
+}
+
+srw_status srw_joint_layout(srw_handle h, int* n_columns, int* source, int* bin) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!n_columns) return fail(h, SRW_EINVAL, "n_columns is NULL");
+  *n_columns = h->n_t;
+  for (int c = 0; c < h->n_t; ++c) {
+    if (source) source[c] = h->joint ? h->col_src[c] : 0;
+    if (bin) bin[c] = h->joint ? h->col_bin[c] : c;
+  }
+  return SRW_OK;
 }
 
 srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, int n_bkg,
@@ -582,7 +837,17 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
   const bool dev = where == SRW_DEVICE;
   const int n_out = stage <= 1 ? h->n_t : h->n_rec;
   float* dst = dev ? out : (stage == 0 ? h->d_S : stage == 1 ? h->d_W : stage == 2 ? h->d_musig : h->d_mu);
-  if (stage == 0) {
+  if (h->joint) {
+    // per-component spectra / weights on the concatenated axis from the FP64
+    // coefficient spectra; the fold of the weights' deviation from the reference
+    if (stage <= 1) {
+      SRW_CUDA(h, launch_basis_eval(h, th, stage, dst, s), "spectrum kernel");
+    } else {
+      SRW_CUDA(h, launch_weights_from_basis(h, th, h->d_W, s), "weights kernel");
+      SRW_CUDA(h, launch_fold_point(h, h->d_W, stage == 2 ? dst : nullptr, stage == 3 ? dst : nullptr, nullptr, s, true),
+               "fold kernel");
+    }
+  } else if (stage == 0) {
     SRW_CUDA(h, launch_spectrum_point(h, th, dst, nullptr, nullptr, s), "spectrum kernel");
   } else {
     // stage 1 returns the full W; stages 2 and 3 fold the deviation from the reference point
@@ -628,7 +893,8 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   if (points_only) {
     st = run_graph(h, 3, precision, P, th, o, s, [&](cudaStream_t cs) {
       for (int p = 0; p < P; ++p) {
-        cudaError_t e = launch_spectrum_point(h, th + 5 * (size_t)p, nullptr, h->d_W, nullptr, cs, true);
+        cudaError_t e = h->joint ? launch_weights_from_basis(h, th + 5 * (size_t)p, h->d_W, cs)
+                                 : launch_spectrum_point(h, th + 5 * (size_t)p, nullptr, h->d_W, nullptr, cs, true);
         if (e != cudaSuccess) return e;
         if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o + p, cs, true)) != cudaSuccess) return e;
       }

@@ -121,6 +121,8 @@ struct srw_ctx {
   double t_min = 1e-3, sin2w = 0.23121, f_tau = 0.5, exposure = 0, lambda = 0, kappa = 0;
   int has_esm_input = 0;
   int has_data = 0;
+  int joint = 0;                   // srw_create_joint: the fold axis is (component, true bin)
+  std::vector<int> col_src, col_bin;  // joint: component and true bin of every column
   unsigned long long version = 0;  // bumped when data or the reference point change
   size_t device_bytes = 0;
 
@@ -211,6 +213,18 @@ cudaError_t launch_spectrum_point(const srw_ctx* h, const float* theta, float* S
 cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s);
 cudaError_t launch_weights_from_basis(const srw_ctx* h, const float* theta, float* W, cudaStream_t s);
 cudaError_t launch_build_shat(srw_ctx* h, cudaStream_t s);
+
+// joint.cu: per-component joint response (eq. Rij) on the concatenated axis.
+// colZ_i = sum_j N_ji / M_j and colY_i = sum_j live_j N_ji / M_j (FP64).
+cudaError_t launch_joint_colsums(const double* hist, const double* mask, const double* live, int n_rec, int n_t,
+                                 double* colZ, double* colY, cudaStream_t s);
+// R[j][col0 + c] = live_j factor N_{j, cols[c]} / M_j, rounded to FP32.
+cudaError_t launch_joint_gather(const double* hist, const double* mask, const double* live, int n_rec, int n_t,
+                                const int* cols, int n_cols, double factor, float* R, int ld, int col0,
+                                cudaStream_t s);
+// Spectra of one point from the FP64 coefficient spectra over the handle's
+// axis: mode 0 S_c(theta), mode 1 W_c = S_c(theta) / S_SM,c E_SM,c (E_SM,c where S_SM,c = 0).
+cudaError_t launch_basis_eval(const srw_ctx* h, const float* theta, int mode, float* out, cudaStream_t s);
 
 // likelihood.cu
 cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStream_t s);

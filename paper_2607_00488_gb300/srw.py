@@ -32,7 +32,7 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
            "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
-           "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled")
+           "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled", "srw_create_joint", "srw_joint_layout")
 
 
 class SrwError(RuntimeError):
@@ -54,6 +54,13 @@ class _Source(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("sin2w", ctypes.c_double), ("f_tau", ctypes.c_double), ("exposure", ctypes.c_double),
                 ("e_true_sm", ctypes.POINTER(ctypes.c_double))]
+
+
+class _JointResponse(ctypes.Structure):
+    _fields_ = [("hist", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("mask", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("scale", ctypes.POINTER(ctypes.c_double)), ("live", ctypes.POINTER(ctypes.c_double)),
+                ("events", ctypes.POINTER(ctypes.c_double))]
 
 
 class _Info(ctypes.Structure):
@@ -96,6 +103,9 @@ def lib():
         vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
         L.srw_create.argtypes = [ctypes.POINTER(_Binning), ctypes.POINTER(_Source), ip, vp,
                                  ctypes.POINTER(_Options), ctypes.POINTER(vp)]
+        L.srw_create_joint.argtypes = [ctypes.POINTER(_Binning), ctypes.POINTER(_Source), ip,
+                                       ctypes.POINTER(_JointResponse), ctypes.POINTER(_Options), ctypes.POINTER(vp)]
+        L.srw_joint_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.srw_set_data.argtypes = [vp, dp, dp, ip, vp]
         L.srw_spectrum.argtypes = [vp, fp, ip, fp, ip, vp]
         L.srw_loglik.argtypes = [vp, fp, ip, vp, ip, ip, vp]
@@ -175,13 +185,7 @@ def _stream(stream):
 
 
 # ------------------------------------------------------------------ entry points
-def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False, sin2w=0.23121, f_tau=0.5,
-               e_true_sm=None):
-    """Create a context (see srw_create in include/srw.h).  Returns the handle."""
-    L = lib()
-    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
-    R = np.ascontiguousarray(R, dtype=np.float32)
-    keep = [t_edges, R]
+def _sources(sources, keep):
     srcs = (_Source * len(sources))()
     for k, s in enumerate(sources):
         e = np.ascontiguousarray(s["e"], dtype=np.float64)
@@ -189,6 +193,17 @@ def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False,
         p = np.ascontiguousarray(s["pee"], dtype=np.float64)
         keep += [e, w, p]
         srcs[k] = _Source(e.size, _dptr(e), _dptr(w), _dptr(p))
+    return srcs
+
+
+def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False, sin2w=0.23121, f_tau=0.5,
+               e_true_sm=None):
+    """Create a context (see srw_create in include/srw.h).  Returns the handle."""
+    L = lib()
+    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    keep = [t_edges, R]
+    srcs = _sources(sources, keep)
     b = _Binning(t_edges.size - 1, _dptr(t_edges), int(n_rec), float(t_min), 1 if midpoint else 0)
     esm = None
     if e_true_sm is not None:
@@ -200,6 +215,55 @@ def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False,
                       ctypes.byref(h))
     _check(st, None)
     return h
+
+
+def srw_create_joint(t_edges, components, hist, exposure, mask=None, scale=None, live=None, events=None, t_min=1e-3,
+                     midpoint=False, sin2w=0.23121, f_tau=0.5):
+    """Create a context with one joint response per component (see
+    srw_create_joint in include/srw.h): hist[k] is component k's [n_rec, n_t]
+    Monte Carlo histogram, mask[k] its live-time correction (or None)."""
+    L = lib()
+    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
+    keep = [t_edges]
+    srcs = _sources(components, keep)
+    n_src = len(components)
+    hs = [np.ascontiguousarray(x, dtype=np.float64) for x in hist]
+    if len(hs) != n_src:
+        raise ValueError("one histogram per component")
+    n_rec = hs[0].shape[0]
+    keep += hs
+    dpp = ctypes.POINTER(ctypes.c_double)
+    harr = (dpp * n_src)(*[_dptr(x) for x in hs])
+    marr = None
+    if mask is not None:
+        ms = [None if m is None else np.ascontiguousarray(m, dtype=np.float64) for m in mask]
+        keep += [m for m in ms if m is not None]
+        marr = (dpp * n_src)(*[None if m is None else _dptr(m) for m in ms])
+
+    def opt(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return _dptr(a)
+    jr = _JointResponse(harr, marr, opt(scale), opt(live), opt(events))
+    b = _Binning(t_edges.size - 1, _dptr(t_edges), int(n_rec), float(t_min), 1 if midpoint else 0)
+    o = _Options(float(sin2w), float(f_tau), float(exposure), None)
+    h = ctypes.c_void_p()
+    st = L.srw_create_joint(ctypes.byref(b), srcs, n_src, ctypes.byref(jr), ctypes.byref(o), ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def srw_joint_layout(h):
+    """(component, true bin) of every column of the fold axis, as two int arrays."""
+    n = ctypes.c_int()
+    _check(lib().srw_joint_layout(h, ctypes.byref(n), None, None), h)
+    src = np.empty(n.value, dtype=np.int32)
+    b = np.empty(n.value, dtype=np.int32)
+    _check(lib().srw_joint_layout(h, ctypes.byref(n), src.ctypes.data_as(ctypes.c_void_p),
+                                  b.ctypes.data_as(ctypes.c_void_p)), h)
+    return src, b
 
 
 def srw_set_data(h, counts, bkg=None, mask=None):
@@ -526,12 +590,20 @@ def srw_destroy(h):
 
 # ------------------------------------------------------------------ convenience
 class Likelihood:
-    """Owns one srw context built from a workload dict (see ``workloads``)."""
+    """Owns one srw context built from a workload dict (see ``workloads``):
+    a conditional response ``R`` (srw_create), or per-component Monte Carlo
+    histograms ``hist`` (srw_create_joint)."""
 
     def __init__(self, wl, counts=None, midpoint=False, e_true_sm=None, mask=None):
-        self.handle = srw_create(wl["t_edges"], wl["R"].shape[0], wl["sources"], wl["R"], wl["exposure"],
-                                 t_min=wl["t_min"], midpoint=midpoint, sin2w=wl["sin2w"], f_tau=wl["f_tau"],
-                                 e_true_sm=e_true_sm)
+        if "hist" in wl:
+            self.handle = srw_create_joint(wl["t_edges"], wl["components"], wl["hist"], wl["exposure"],
+                                           mask=wl.get("mc_mask"), scale=wl.get("scale"), live=wl.get("live"),
+                                           events=wl.get("events"), t_min=wl["t_min"], midpoint=midpoint,
+                                           sin2w=wl["sin2w"], f_tau=wl["f_tau"])
+        else:
+            self.handle = srw_create(wl["t_edges"], wl["R"].shape[0], wl["sources"], wl["R"], wl["exposure"],
+                                     t_min=wl["t_min"], midpoint=midpoint, sin2w=wl["sin2w"], f_tau=wl["f_tau"],
+                                     e_true_sm=e_true_sm)
         if counts is not None:
             srw_set_data(self.handle, counts, wl.get("bkg"), mask)
 
@@ -558,6 +630,9 @@ class Likelihood:
 
     def basis(self):
         return srw_get_basis(self.handle)
+
+    def layout(self):
+        return srw_joint_layout(self.handle)
 
     def info(self):
         return srw_info(self.handle)

@@ -80,3 +80,35 @@ def test_group_create_rejects_invalid_arguments(srw, handles, P):
     with pytest.raises(srw.SrwError) as ei:
         srw.srw_group_create(handles, P)
     assert ei.value.status == 1  # SRW_EINVAL, raised before any device call
+
+
+def _joint(**kw):
+    a = {
+        "t_edges": np.linspace(0.0, 1.0, 9),
+        "components": [{"e": np.array([0.862]), "w": np.array([1.0]), "pee": np.array([0.55])}],
+        "hist": [np.full((4, 8), 3.0)],
+        "exposure": 100.0,
+    }
+    a.update(kw)
+    return a
+
+
+@pytest.mark.parametrize("bad", [
+    {"hist": [np.full((4, 8), -1.0)]},                       # negative histogram
+    {"hist": [np.full((4, 8), np.nan)]},                     # NaN histogram
+    {"mask": [np.zeros(4)]},                                 # live-time correction 0
+    {"scale": np.array([0.0])},
+    {"events": np.array([-5.0])},
+    {"live": np.array([1.0, -1.0, 1.0, 1.0])},
+    {"exposure": np.inf},
+    {"t_edges": np.array([0.0, 0.5, 0.4, 1.0])},
+])
+def test_create_joint_rejects_invalid_arguments(srw, bad):
+    a = _joint(**bad)
+    t = a.pop("t_edges")
+    comps, hist, expo = a.pop("components"), a.pop("hist"), a.pop("exposure")
+    if len(t) != 9:
+        hist = [np.full((4, len(t) - 1), 3.0)]
+    with pytest.raises(srw.SrwError) as ei:
+        srw.srw_create_joint(t, comps, hist, expo, **a)
+    assert ei.value.status == 1  # SRW_EINVAL, raised before any device call
