@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--train-points", type=int, default=1_000_000, help="exact-path spectra the surrogate trains on")
     ap.add_argument("--scan-points", type=int, default=100_000_000, help="Sobol points of the pre-screened scan")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate training epochs")
+    ap.add_argument("--no-joint", action="store_true", help="skip the per-component joint-response measurement")
     ap.add_argument("--groups", type=int, default=64, help="configurations of the grouped workload")
     ap.add_argument("--group-scale", type=float, default=1.0,
                     help="size factor of the grouped workload (profiling captures of a smaller case)")
@@ -298,16 +299,19 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
         counts = workloads.load_group_counts(gw)
     else:  # smaller profiling cases: flat pseudo-data (the fold does the same work for any counts)
         counts = [workloads.poisson_counts(np.full(s["n_rec"], s["exposure"] / s["n_rec"]), 0) for s in gw["groups"]]
-    members, thetas, useful = [], [], 0.0
+    members, thetas, dense = [], [], 0.0
     for g, spec in enumerate(gw["groups"]):
         wl = workloads.uneven_group_inputs(gw, g)
         members.append(srw.Likelihood(wl, counts[g]))
         thetas.append(wl["theta"])
-        useful += 2.0 * spec["n_rec"] * spec["n_t"] * spec["p"]
+        dense += 2.0 * spec["n_rec"] * spec["n_t"] * spec["p"]
     P = [spec["p"] for spec in gw["groups"]]
     grp = srw.GroupedLikelihood(members, P)
     cand = grp.autotune(prec)
     sched = grp.schedule(prec)
+    # useful flops on the K blocks the fold executes (each configuration at its scheduled tile width)
+    useful = sum(2.0 * spec["n_rec"] * spec["n_t"] * spec["p"] * m.fold_work(prec, bn)
+                 for spec, m, bn in zip(gw["groups"], members, sched["bn"]))
     th = torch.tensor(np.concatenate(thetas), device=dev)
     out = torch.empty(th.shape[0], dtype=torch.float64, device=dev)
     grp.profile(True)
@@ -337,6 +341,7 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
         "roofline": {"bound": "tensor", "achieved": useful / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": useful / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel (grouped)",
                      "useful_tflop_per_launch": useful / 1e12, "fold_ms": statistics.mean(fold_ms),
+                     "executed_block_fraction": useful / dense, "dense_equivalent_tflops": dense / fold_s / 1e12,
                      "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec])},
         "schedule": {"candidate": cand, "bn_max": sched["bn_max"], "items": sched["n_items"], "ctas": sched["n_cta"],
                      "configs_bn128": sum(1 for b in sched["bn"] if b == 128)},
@@ -344,6 +349,51 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
     grp.close()
     for m in members:
         m.close()
+    return res
+
+
+# --------------------------------------------------------------------------- joint response
+def joint_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src):
+    """The solar set with one Monte Carlo joint response per component (six
+    components, 1e7 SM events each; eqs. Rij, fNp_reweight): one fold over the
+    concatenated (component, true bin) axis for the same 65,536 points."""
+    import torch
+
+    wl = workloads.solar_joint_workload(p=args.points, theta_seed=3)
+    lk = srw.Likelihood(wl, workloads.load_counts(wl["name"]))
+    info = lk.info()
+    srw.srw_autotune(lk.handle, args.points, prec)
+    th = torch.tensor(wl["theta"], device=dev)
+    out = torch.empty(args.points, dtype=torch.float64, device=dev)
+    srw.srw_profile(lk.handle, True)
+    for _ in range(args.warmup):
+        flush.add_(1.0)
+        lk.loglik(th, prec, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms, fold_ms = [], []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        lk.loglik(th, prec, out=out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        fold_ms.append(srw.srw_profile_read(lk.handle))
+    srw.srw_profile(lk.handle, False)
+    work = lk.fold_work(prec)
+    dense = 2.0 * info["n_rec"] * info["n_t"] * args.points
+    fold_s = statistics.mean(fold_ms) * 1e-3
+    peak = peaks["bf16_tflops"] / PRODUCTS[prec]
+    res = {"workload": "solar joint response, 6 components x 1e7 MC events, 4096 x 2048 bins",
+           "fold_axis": info["n_t"], "points": args.points,
+           "evals_s": args.points * args.steps / (sum(step_ms) * 1e-3), "ms_per_step": statistics.mean(step_ms),
+           "roofline": {"bound": "tensor", "achieved": dense * work / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": dense * work / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel",
+                        "executed_block_fraction": work, "fold_ms": statistics.mean(fold_ms),
+                        "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec])}}
+    lk.close()
     return res
 
 
@@ -482,7 +532,11 @@ def main():
     # roofline of the fold kernel (useful flops 2 N_rec N_T per point)
     peaks, peak_src = measured_peaks()
     fold_avg_s = statistics.mean(fold_ms) * 1e-3
-    useful = 2.0 * info["n_rec"] * info["n_t"] * P
+    # useful flops 2 N_rec N_T per point on the (rec tile, K block) pairs the
+    # fold executes: blocks where the split response is all zero are skipped
+    work = lk.fold_work(prec)
+    dense = 2.0 * info["n_rec"] * info["n_t"] * P
+    useful = dense * work
     if prec == srw.SRW_FP32:
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, kernel_file, tag = "alu", "paper_2607_00488_gb300/csrc/fold_simt.cu", "fold_simt_kernel"
@@ -498,7 +552,8 @@ def main():
                 "traffic": recorded_traffic(kernel_file, tag + ":" + prec_name),
                 "kernel": tag,
                 "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec]),
-                "executed_tflops": executed / fold_avg_s / 1e12, "fold_ms": statistics.mean(fold_ms)}
+                "executed_tflops": executed / fold_avg_s / 1e12, "fold_ms": statistics.mean(fold_ms),
+                "executed_block_fraction": work, "dense_equivalent_tflops": dense / fold_avg_s / 1e12}
 
     # the other tensor-core split timed the same way (reported beside the headline)
     alt = {}
@@ -524,7 +579,8 @@ def main():
         alt_name = {v: k for k, v in srw.PRECISIONS.items()}[alt_prec]
         alt = {"precision": alt_name, "value": P * args.steps / (sum(a_ms) * 1e-3), "ms_per_step": statistics.mean(a_ms),
                "fold_ms": statistics.mean(a_fold),
-               "frac": useful / a_fold_s / 1e12 / (peaks["bf16_tflops"] / PRODUCTS[alt_prec])}
+               "executed_block_fraction": lk.fold_work(alt_prec),
+               "frac": dense * lk.fold_work(alt_prec) / a_fold_s / 1e12 / (peaks["bf16_tflops"] / PRODUCTS[alt_prec])}
 
     # the exact rank-8 evaluator on the same batch (disclosed beside the fold;
     # same -2 ln L, no contraction over the true bins)
@@ -605,6 +661,8 @@ def main():
         line["clocks"] = clk
     if world == 1 and not args.no_grouped and prec != srw.SRW_FP32:
         line["grouped"] = grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)
+    if world == 1 and not args.no_joint and prec != srw.SRW_FP32:
+        line["joint"] = joint_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, peak_src)
     if world == 1 and not args.no_surrogate and info["tensor_path"]:
         line["surrogate"] = surrogate_measurement(args, srw, workloads, lk, peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -261,6 +261,16 @@ srw_status srw_get_basis(srw_handle h, double* out);
 srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char* cache_path,
                         void* stream, int* chosen);
 
+/* Work of the batched tensor-core fold at `precision` with rec tiles of
+ * `tile` bins (128 or 256; 0 = the handle's current configuration):
+ * *executed_fraction receives the fraction of the (rec tile, block of 64 true
+ * bins) pairs it executes.  Per rec tile the fold
+ * runs only the range of true-bin blocks in which the split response has a
+ * nonzero element; the skipped blocks hold zeros in both split operands, so
+ * their products are exact zeros and skipping them changes no bit of the
+ * result.  1 for SRW_FP32 (the SIMT fold runs every block). */
+srw_status srw_fold_work(srw_handle h, srw_precision precision, int tile, double* executed_fraction);
+
 /* Sizes of a context. */
 typedef struct {
   int n_t, n_rec, n_nodes, k_pad;

@@ -155,9 +155,11 @@ struct TcLaunch {
 template <bool GROUPED, int BN>
 __device__ __forceinline__ TcGroup work_at(const TcLaunch& L, int idx, int& m0, int& n0, int& gi) {
   if (!GROUPED) {
-    const int nt = L.g0.n_tiles;
-    m0 = (idx / nt) * kBM;
-    n0 = (idx % nt) * BN;
+    // rec-tile-major: the grid stride walks every CTA across all rec tiles,
+    // whose K-block ranges (and so costs) differ
+    const int mt = (L.g0.P + kBM - 1) / kBM;
+    m0 = (idx % mt) * kBM;
+    n0 = (idx / mt) * BN;
     gi = 0;
     return L.g0;
   }
@@ -251,7 +253,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
       const float* theta = L.theta + (size_t)G.p_off * 5;
       const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
-      const int n_kb = G.k_pad / kBK;
+      // K blocks of this rec tile that hold nonzero response (the rest add exact zeros)
+      const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
       float c[4][kNB], sc[4];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
@@ -266,7 +269,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         }
       }
       bool ok = true;
-      for (int kb = 0; kb < n_kb; ++kb, ++g) {
+      for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
         const int st = g % ST, sl = g % kShatSlots;
         // the A buffers of this stage are free once the MMAs of its previous
         // use have completed; the coefficient spectra come through their own ring
@@ -396,7 +399,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int n_kb = G.k_pad / kBK;
+        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
         const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * kBK * 2);
         const CUtensorMap* mh = &map_hi;
         const CUtensorMap* ml = &map_lo;
@@ -409,7 +412,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             map_fenced[gi >> 5] |= 1u << (gi & 31);
           }
         }
-        for (int kb = 0; kb < n_kb; ++kb, ++g) {
+        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
           const int st = g % ST;
           if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
             give_up();
@@ -433,8 +436,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int n_kb = G.k_pad / kBK;
-        for (int kb = 0; kb < n_kb; ++kb, ++g) {
+        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
+        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
           const int sl = g % kShatSlots;
           if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
             give_up();
@@ -461,7 +464,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int n_kb = G.k_pad / kBK;
+        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
         const uint32_t idesc = idesc_f16kind(kBM, GROUPED ? G.bn : BN, F16);
         const int buf = tc & 1;
         if (!ptx::mbar_wait(&acc_empty[buf], ((tc >> 1) & 1) ^ 1, &abort_flag)) {
@@ -471,7 +474,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
         bool ok = true;
-        for (int kb = 0; kb < n_kb; ++kb, ++g) {
+        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
           const int st = g % ST;
           if (!ptx::mbar_wait(&r_full[st], (g / ST) & 1, &abort_flag) ||
               !ptx::mbar_wait(&w_full[st], (g / ST) & 1, &abort_flag)) {
@@ -485,7 +488,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
 #pragma unroll
           for (int ks = 0; ks < kBK / 16; ++ks) {
             const uint32_t off = (uint32_t)ks * 32u;  // 16 BF16 along K inside the swizzle atom
-            mma_bf16(d_tmem, smem_desc_sw128(ah + off), smem_desc_sw128(bh + off), idesc, (kb | ks) != 0);
+            mma_bf16(d_tmem, smem_desc_sw128(ah + off), smem_desc_sw128(bh + off), idesc, (kb != kr.x) || ks != 0);
             if (X3) {
               mma_bf16(d_tmem, smem_desc_sw128(ah + off), smem_desc_sw128(bl + off), idesc, 1u);
               mma_bf16(d_tmem, smem_desc_sw128(al + off), smem_desc_sw128(bh + off), idesc, 1u);
@@ -582,6 +585,35 @@ __global__ void shat_k8_kernel(const float* __restrict__ shat, int k_pad, float*
   if (k >= k_pad) return;
 #pragma unroll
   for (int b = 0; b < kNB; ++b) out[(size_t)k * kNB + b] = shat[(size_t)b * k_pad + k];
+}
+
+// K-block range {first, end} of each rec tile of width bn: the blocks of 64
+// true bins in which some row of the tile has a nonzero hi or lo element.
+// Outside the range every product is an exact zero, so the folds skip those
+// blocks without changing a bit of the accumulation.  A tile without any
+// nonzero element keeps one block (its accumulator must still be written).
+__global__ void kb_range_kernel(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
+                                int n_rec, int k_pad, int bn, int2* __restrict__ out) {
+  __shared__ int first, last;
+  if (threadIdx.x == 0) {
+    first = 1 << 30;
+    last = -1;
+  }
+  __syncthreads();
+  const int r0 = blockIdx.x * bn, r1 = min(r0 + bn, n_rec);
+  int f = 1 << 30, l = -1;
+  for (int r = r0; r < r1; ++r)
+    for (int k = threadIdx.x; k < k_pad; k += blockDim.x) {
+      const size_t q = (size_t)r * k_pad + k;
+      if (((hi[q] | lo[q]) & 0x7fffu) != 0u) {  // +-0 adds nothing
+        f = min(f, k / kBK);
+        l = max(l, k / kBK);
+      }
+    }
+  atomicMin(&first, f);
+  atomicMax(&last, l);
+  __syncthreads();
+  if (threadIdx.x == 0) out[blockIdx.x] = last < 0 ? make_int2(0, 1) : make_int2(first, last + 1);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -694,8 +726,36 @@ void tc_release(srw_ctx* h) {
   h->tmap = nullptr;
 }
 
-TcGroup tc_group_of(const srw_ctx* h, int bn) {
+cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s) {
+  for (int f16 = 0; f16 < 2; ++f16)
+    for (int bi = 0; bi < 2; ++bi) {
+      const int bn = bi ? 256 : 128, n_tiles = (h->n_rec + bn - 1) / bn;
+      cudaError_t e = cudaMalloc(&h->d_kbr[f16][bi], sizeof(int2) * n_tiles);
+      if (e != cudaSuccess) return e;
+      h->device_bytes += sizeof(int2) * n_tiles;
+      const unsigned short* hi = reinterpret_cast<const unsigned short*>(f16 ? (const void*)h->d_rhi16 : (const void*)h->d_rhi);
+      const unsigned short* lo = reinterpret_cast<const unsigned short*>(f16 ? (const void*)h->d_rlo16 : (const void*)h->d_rlo);
+      kb_range_kernel<<<n_tiles, 256, 0, s>>>(hi, lo, h->n_rec, h->k_pad, bn, h->d_kbr[f16][bi]);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      h->kbr_h[f16][bi].resize(n_tiles);
+      e = cudaMemcpyAsync(h->kbr_h[f16][bi].data(), h->d_kbr[f16][bi], sizeof(int2) * n_tiles, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaStreamSynchronize(s);
+}
+
+double tc_block_fraction(const srw_ctx* h, int bn, bool f16) {
+  const std::vector<int2>& r = h->kbr_h[f16 ? 1 : 0][bn == 256 ? 1 : 0];
+  const int n_kb = h->k_pad / kBK;
+  if (r.empty() || n_kb == 0) return 1.0;
+  double used = 0.0;
+  for (const int2& t : r) used += t.y - t.x;
+  return used / ((double)r.size() * n_kb);
+}
+
+TcGroup tc_group_of(const srw_ctx* h, int bn, bool f16) {
   TcGroup G{};
+  G.kbr = h->d_kbr[f16 ? 1 : 0][bn == 256 ? 1 : 0];
   G.map_hi = G.map_lo = nullptr;
   G.shat_k8 = reinterpret_cast<const float4*>(h->d_shat_k8);
   G.nb2 = reinterpret_cast<const float2*>(h->d_nb2);
@@ -723,7 +783,7 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   const int bn = cfg.bn == 256 ? 256 : 128, bi = bn == 256 ? 1 : 0;
   const bool f16 = precision == SRW_FP16X3;
   TcLaunch L{};
-  L.g0 = tc_group_of(h, bn);
+  L.g0 = tc_group_of(h, bn, f16);
   L.g0.P = P;
   L.groups = nullptr;
   L.items = nullptr;

@@ -155,7 +155,16 @@ srw_status ensure_parts(srw_group g, size_t n) {
 }
 
 // Tile widths of one candidate schedule.
-void candidate_widths(srw_group g, int cand, int* bn_max, std::vector<int>& bn) {
+// Cost of all rec tiles of handle h at width bn: each tile runs only its
+// K-block range.
+double tiles_cost(const srw_ctx* h, int bn, bool f16) {
+  const std::vector<int2>& r = h->kbr_h[f16 ? 1 : 0][bn == 256 ? 1 : 0];
+  double c = 0.0;
+  for (const int2& t : r) c += item_cost(t.y - t.x, bn);
+  return c;
+}
+
+void candidate_widths(srw_group g, int cand, bool f16, int* bn_max, std::vector<int>& bn) {
   bn.assign(g->n, 256);
   *bn_max = 256;
   if (cand == 2) {
@@ -165,10 +174,7 @@ void candidate_widths(srw_group g, int cand, int* bn_max, std::vector<int>& bn) 
   }
   if (cand == 1) {
     for (int i = 0; i < g->n; ++i) {
-      const int n_rec = g->hs[i]->n_rec, n_kb = g->hs[i]->k_pad / kBK;
-      const double c256 = ((n_rec + 255) / 256) * item_cost(n_kb, 256);
-      const double c128 = ((n_rec + 127) / 128) * item_cost(n_kb, 128);
-      bn[i] = c128 < c256 ? 128 : 256;
+      bn[i] = tiles_cost(g->hs[i], 128, f16) < tiles_cost(g->hs[i], 256, f16) ? 128 : 256;
     }
   }
 }
@@ -177,7 +183,8 @@ srw_status build_plan(srw_group g, int pi, int cand) {
   srw_group_plan& pl = g->plan[pi];
   free_plan(pl);
   pl.candidate = cand;
-  candidate_widths(g, cand, &pl.bn_max, pl.bn);
+  const bool f16 = pi + 1 == SRW_FP16X3;
+  candidate_widths(g, cand, f16, &pl.bn_max, pl.bn);
 
   struct Item {
     double cost;
@@ -191,19 +198,21 @@ srw_status build_plan(srw_group g, int pi, int cand) {
   for (int i = 0; i < g->n; ++i) {
     const srw_ctx* h = g->hs[i];
     const int bn = pl.bn[i];
-    TcGroup G = srw::tc_group_of(h, bn);
+    TcGroup G = srw::tc_group_of(h, bn, f16);
     G.P = g->P[i];
     G.p_off = g->p_off[i];
     G.parts_off = parts_off;
     desc[i] = G;
     gparts[i] = GroupPart{parts_off, G.n_tiles, G.P, G.p_off, 0, h->d_cdata};
     parts_off += (long long)G.n_tiles * G.P;
-    const cudaError_t e = srw::tc_encode_maps(h, bn, pi + 1 == SRW_FP16X3, &maps[2 * (size_t)i], &maps[2 * (size_t)i + 1]);
+    const cudaError_t e = srw::tc_encode_maps(h, bn, f16, &maps[2 * (size_t)i], &maps[2 * (size_t)i + 1]);
     if (e != cudaSuccess) return gcuda(g, e, "tensor maps");
-    const double cost = item_cost(h->k_pad / kBK, bn);
+    const std::vector<int2>& kr = h->kbr_h[f16 ? 1 : 0][bn == 256 ? 1 : 0];
     const int m_tiles = (G.P + kBM - 1) / kBM;
-    for (int nt = 0; nt < G.n_tiles; ++nt)
+    for (int nt = 0; nt < G.n_tiles; ++nt) {
+      const double cost = item_cost(kr[nt].y - kr[nt].x, bn);
       for (int mt = 0; mt < m_tiles; ++mt) all.push_back({cost, i, mt * kBM, nt * bn});
+    }
   }
   // longest first; equal costs keep (configuration, rec tile, point tile) order
   std::stable_sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });

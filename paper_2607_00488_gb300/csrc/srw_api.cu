@@ -127,6 +127,8 @@ static void release(srw_ctx* h) {
   tc_release(h);
   dfree(h->d_node_a); dfree(h->d_node_w); dfree(h->d_node_c); dfree(h->d_node_wlo); dfree(h->d_shat_lo); dfree(h->d_shat_k8); dfree(h->d_node64); dfree(h->d_bin_count); dfree(h->d_bin_f);
   dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis); dfree(h->d_ssm64); dfree(h->d_esm64);
+  for (int f = 0; f < 2; ++f)
+    for (int b = 0; b < 2; ++b) dfree(h->d_kbr[f][b]);
   dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
@@ -719,7 +721,7 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
       }
     }
     CREATE_CUDA(launch_split_r(h, s), "split R");
-    CREATE_CUDA(cudaStreamSynchronize(s), "split sync");
+    CREATE_CUDA(tc_block_ranges(h, s), "K-block ranges");
     CREATE_CUDA(tc_prepare(h), "tensor map encode");
     h->tensor_ok = true;
   }
@@ -1093,6 +1095,17 @@ srw_status srw_get_basis(srw_handle h, double* out) {
   if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
   if (!out) return fail(h, SRW_EINVAL, "out is NULL");
   SRW_CUDA(h, cudaMemcpy(out, h->d_basis, sizeof(double) * kNB * (size_t)h->n_t, cudaMemcpyDeviceToHost), "download");
+  return SRW_OK;
+}
+
+srw_status srw_fold_work(srw_handle h, srw_precision precision, int tile, double* executed_fraction) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!executed_fraction) return fail(h, SRW_EINVAL, "executed_fraction is NULL");
+  if (precision < SRW_FP32 || precision > SRW_FP16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (tile != 0 && tile != 128 && tile != 256) return fail(h, SRW_EINVAL, "tile must be 0, 128 or 256");
+  *executed_fraction = 1.0;
+  if (precision != SRW_FP32 && h->tensor_ok)
+    *executed_fraction = tc_block_fraction(h, tile ? tile : h->cfg[precision].bn, precision == SRW_FP16X3);
   return SRW_OK;
 }
 

@@ -91,6 +91,7 @@ struct TcGroup {
   float sin2w_hi, sin2w_lo;
   CoefRef cref;
   const float* rinv;           // SRW_FP16X3: [n_rec] inverse power-of-two row scales of R
+  const int2* kbr;             // [n_tiles] K-block range {first, end} holding the tile's nonzero response
   float wmax[kNB];             // SRW_FP16X3: max_i |shat_b,i| (bound of the weighted-spectrum deviations)
 };
 
@@ -150,6 +151,8 @@ struct srw_ctx {
   __half* d_rhi16 = nullptr;       // [rec_pad][k_pad] FP16 split of R scaled by row (SRW_FP16X3)
   __half* d_rlo16 = nullptr;
   float* d_rinv = nullptr;         // [n_rec] inverse row scales of the FP16 split
+  int2* d_kbr[2][2] = {};          // [FP16 split?][bn == 256] K-block range of each rec tile
+  std::vector<int2> kbr_h[2][2];   // host copies (grouped scheduling, work accounting)
   float wmax[8] = {};              // max_i |shat_b,i|
   float* d_wscale = nullptr;       // [P] per-point scales of the FP16 split (batched scratch)
   double* d_linM = nullptr;        // [n_rec][8] M = R shat^T (FP64) of the rank-8 evaluator
@@ -262,8 +265,14 @@ cudaError_t launch_linear_profiled(const srw_ctx* h, const float* theta, int P, 
 cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
                                 cudaStream_t s);
 int tc_max_groups();
-// Descriptor of handle h as a configuration with rec tile bn (maps left null).
-TcGroup tc_group_of(const srw_ctx* h, int bn);
+// Descriptor of handle h as a configuration with rec tile bn (maps left null)
+// for the FP16 split (f16) or the BF16 split.
+TcGroup tc_group_of(const srw_ctx* h, int bn, bool f16);
+// Per rec tile, the K blocks where the split response has nonzero elements
+// (both splits, both tile widths); blocks outside hold only zeros.
+cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s);
+// Fraction of the (rec tile, K block) pairs a batched fold executes.
+double tc_block_fraction(const srw_ctx* h, int bn, bool f16);
 // Tensor maps of h's hi / lo response (FP16 split if f16, else BF16) with a
 // box of 64 K x bn rows.
 cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo);

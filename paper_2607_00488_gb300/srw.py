@@ -32,7 +32,8 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_surrogate_get_weights", "srw_surrogate_forward", "srw_surrogate_gradients", "srw_surrogate_train_step",
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
            "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
-           "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled", "srw_create_joint", "srw_joint_layout")
+           "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled", "srw_create_joint", "srw_joint_layout",
+           "srw_fold_work")
 
 
 class SrwError(RuntimeError):
@@ -106,6 +107,7 @@ def lib():
         L.srw_create_joint.argtypes = [ctypes.POINTER(_Binning), ctypes.POINTER(_Source), ip,
                                        ctypes.POINTER(_JointResponse), ctypes.POINTER(_Options), ctypes.POINTER(vp)]
         L.srw_joint_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp]
+        L.srw_fold_work.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_double)]
         L.srw_set_data.argtypes = [vp, dp, dp, ip, vp]
         L.srw_spectrum.argtypes = [vp, fp, ip, fp, ip, vp]
         L.srw_loglik.argtypes = [vp, fp, ip, vp, ip, ip, vp]
@@ -397,6 +399,14 @@ def srw_autotune(h, P, precision, cache_path=None, stream=None):
     return chosen.value
 
 
+def srw_fold_work(h, precision, tile=0):
+    """Fraction of the (rec tile, K block) pairs the batched fold executes
+    (tile 0: the handle's configured rec-tile width)."""
+    f = ctypes.c_double()
+    _check(lib().srw_fold_work(h, int(precision), int(tile), ctypes.byref(f)), h)
+    return f.value
+
+
 def srw_info(h):
     i = _Info()
     _check(lib().srw_info(h, ctypes.byref(i)), h)
@@ -633,6 +643,9 @@ class Likelihood:
 
     def layout(self):
         return srw_joint_layout(self.handle)
+
+    def fold_work(self, precision, tile=0):
+        return srw_fold_work(self.handle, precision, tile)
 
     def info(self):
         return srw_info(self.handle)

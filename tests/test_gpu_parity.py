@@ -365,3 +365,43 @@ def test_profiled_asimov_recovers_the_normalisation(srw, be7):
         v, a = lk.loglik_profiled(theta0[None, :].astype(np.float32))
     assert a[0] == pytest.approx(1.3, rel=1e-5)
     assert v[0] == pytest.approx(data_constant(counts), abs=1e-3)
+
+
+# ---------------------------------------------------------------- skipped zero blocks
+def _split_nonzero(R, f16):
+    """Host emulation of the response splits: which elements have a nonzero hi
+    or lo part (FP16: rows scaled by 2^(14 - e), e the binary exponent of the
+    row maximum; BF16: unscaled)."""
+    from workloads.mlp import round_to_bf16
+    R = np.asarray(R, np.float32)
+    if f16:
+        m = np.abs(R).max(axis=1)
+        e = np.frexp(m)[1]
+        x = R * np.ldexp(np.float32(1.0), 14 - e)[:, None].astype(np.float32)
+        hi = x.astype(np.float16)
+        lo = (x - hi.astype(np.float32)).astype(np.float16)
+    else:
+        hi = round_to_bf16(R)
+        lo = round_to_bf16(R - hi)
+    return (hi != 0) | (lo != 0)
+
+
+def _block_fraction(nz, bn, bk=64):
+    n_rec, n_t = nz.shape
+    n_kb = -(-n_t // bk)
+    used = 0
+    for r0 in range(0, n_rec, bn):
+        cols = np.nonzero(nz[r0:r0 + bn].any(axis=0))[0]
+        used += (cols.max() // bk - cols.min() // bk + 1) if cols.size else 1
+    return used / (-(-n_rec // bn) * n_kb)
+
+
+@pytest.mark.parametrize("prec,f16", [("fp16x3", True), ("bf16x3", False)])
+@pytest.mark.parametrize("bn", [128, 256])
+def test_skipped_blocks_are_the_zero_blocks(srw, solar, prec, f16, bn):
+    # the (rec tile, K block) pairs the tensor-core fold executes are exactly
+    # the ranges that hold nonzero split elements (index work: exact)
+    got = solar.lk.fold_work(srw.PRECISIONS[prec], bn)
+    want = _block_fraction(_split_nonzero(solar.wl["R"], f16), bn)
+    assert got == pytest.approx(want, abs=1e-12), (got, want)
+    assert got < 0.7  # the banded response leaves most blocks empty
