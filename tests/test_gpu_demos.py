@@ -7,6 +7,8 @@ data constant, Gibbs' inequality) and 90 % CL interval edges equal to the
 oracle's scan of the same grid to 1e-3 of the grid range.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -28,10 +30,21 @@ def srw():
     return pkg
 
 
+def _injected():
+    """The paper's injection values (tests/golden/asimov_sec6b.txt)."""
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "asimov_sec6b.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            vals[f[0]] = float(f[1])
+    return vals
+
+
 def test_asimov_injection_recovery(srw):
     from paper_2607_00488_gb300 import demos
     wl = workloads.be7_line_workload()
-    theta_inj = np.array([0.05, 0.0, 0.0, 0.0, 3.0])
+    inj = _injected()
+    theta_inj = np.array([inj["eps_L_ee"], 0.0, 0.0, 0.0, inj["mu_nu_1e-11_muB"]])
     ref = O.OracleModel.from_workload(wl)
     ref.set_data(np.zeros(wl["R"].shape[0]), wl["bkg"])
     counts = ref.mu(theta_inj)  # Asimov data from the oracle
