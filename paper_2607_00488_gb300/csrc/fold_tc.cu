@@ -80,15 +80,22 @@ __device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
 // hi / lo halves of two values: hi = round(x), lo = round(x - hi), packed in pairs.
 template <bool F16>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  // the residuals (a, b) - hi are exact in FP32; one packed subtraction forms both
+  float2 h2;
   if (F16) {
     hi = pack_f16x2(a, b);
-    const __half2 v = *reinterpret_cast<const __half2*>(&hi);
-    lo = pack_f16x2(a - __low2float(v), b - __high2float(v));
+    h2 = __half22float2(*reinterpret_cast<const __half2*>(&hi));
   } else {
     hi = pack_bf16x2(a, b);
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(&hi);
-    lo = pack_bf16x2(a - __low2float(v), b - __high2float(v));
+    h2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hi));
   }
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"((uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32)),
+        "l"((uint64_t)__float_as_uint(h2.x) | ((uint64_t)__float_as_uint(h2.y) << 32)));
+  const float ra = __uint_as_float((uint32_t)r), rb = __uint_as_float((uint32_t)(r >> 32));
+  lo = F16 ? pack_f16x2(ra, rb) : pack_bf16x2(ra, rb);
 }
 
 // Power of two s with s * bound in [2^13, 2^14): the FP16 scale of values
@@ -255,14 +262,17 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
       // K blocks of this rec tile that hold nonzero response (the rest add exact zeros)
       const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
-      float c[4][kNB], sc[4];
+      float c[4][kNB];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int p = m0 + rg + 32 * rr;
-        sc[rr] = 1.f;
         if (p < G.P) {
           coefficients(theta + (size_t)p * 5, s2w, G.cref, c[rr]);
-          if (F16) sc[rr] = L.wscale[(size_t)G.p_off + p];
+          if (F16) {  // the point's power-of-two scale, exact in every product and sum
+            const float sc = L.wscale[(size_t)G.p_off + p];
+#pragma unroll
+            for (int b = 0; b < kNB; ++b) c[rr][b] *= sc;
+          }
         } else {
 #pragma unroll
           for (int b = 0; b < kNB; ++b) c[rr][b] = 0.f;
@@ -298,7 +308,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           }
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
-            if (X3) split2<F16>(w[rr][0] * sc[rr], w[rr][1] * sc[rr], h[rr][q], l[rr][q]);
+            if (X3) split2<F16>(w[rr][0], w[rr][1], h[rr][q], l[rr][q]);
             else h[rr][q] = pack_bf16x2(w[rr][0], w[rr][1]);
           }
         }
@@ -356,26 +366,24 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             dj[k] = j < n_rec ? __ldg(nb2 + j) : make_float2(-1.f, 1.f);  // n_j (-1: masked), b_j + ref
           }
         }
-        float v[16];
+        float v[16], sj[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
-        if (F16) {  // undo the power-of-two scales of both operands
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int j = n0 + c0 + k;
-            v[k] *= sinv * (j < n_rec ? __ldg(rinv + j) : 0.f);
-          }
+        for (int k = 0; k < 16; ++k) {  // the power-of-two scales of both operands (exact)
+          const int j = n0 + c0 + k;
+          sj[k] = F16 ? sinv * (j < n_rec ? __ldg(rinv + j) : 0.f) : 1.f;
         }
         if (musig_out != nullptr && p < P) {  // batched folded spectra (row p)
           float* row = musig_out + (size_t)(G.p_off + p) * n_rec;
 #pragma unroll
           for (int k = 0; k < 16; ++k)
-            if (n0 + c0 + k < n_rec) row[n0 + c0 + k] = v[k];
+            if (n0 + c0 + k < n_rec) row[n0 + c0 + k] = v[k] * sj[k];
         }
         if (parts != nullptr) {
           float ts = 0.f;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const float t = poisson_term_f32_sel(v[k] + dj[k].y, dj[k].x);
+            const float t = poisson_term_f32_sel(F16 ? fmaf(v[k], sj[k], dj[k].y) : v[k] + dj[k].y, dj[k].x);
             ts += dj[k].x >= 0.f ? t : 0.f;  // masked and padding columns add nothing
           }
           if (isinf(ts)) infinite = true;
@@ -587,33 +595,24 @@ __global__ void shat_k8_kernel(const float* __restrict__ shat, int k_pad, float*
   for (int b = 0; b < kNB; ++b) out[(size_t)k * kNB + b] = shat[(size_t)b * k_pad + k];
 }
 
-// K-block range {first, end} of each rec tile of width bn: the blocks of 64
-// true bins in which some row of the tile has a nonzero hi or lo element.
-// Outside the range every product is an exact zero, so the folds skip those
-// blocks without changing a bit of the accumulation.  A tile without any
-// nonzero element keeps one block (its accumulator must still be written).
-__global__ void kb_range_kernel(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
-                                int n_rec, int k_pad, int bn, int2* __restrict__ out) {
-  __shared__ int first, last;
-  if (threadIdx.x == 0) {
-    first = 1 << 30;
-    last = -1;
-  }
-  __syncthreads();
-  const int r0 = blockIdx.x * bn, r1 = min(r0 + bn, n_rec);
-  int f = 1 << 30, l = -1;
-  for (int r = r0; r < r1; ++r)
-    for (int k = threadIdx.x; k < k_pad; k += blockDim.x) {
-      const size_t q = (size_t)r * k_pad + k;
-      if (((hi[q] | lo[q]) & 0x7fffu) != 0u) {  // +-0 adds nothing
-        f = min(f, k / kBK);
-        l = max(l, k / kBK);
-      }
+// Nonzero flags of the (rec tile, K block) pairs of one split: block (kb, t)
+// reads the bn x 64 elements of hi and lo in 16-byte pieces (+-0 counts as
+// zero: it adds nothing).  The host turns the flags into each tile's range.
+__global__ void kb_flags_kernel(const uint4* __restrict__ hi, const uint4* __restrict__ lo, int n_rec, int k_pad,
+                                int bn, unsigned char* __restrict__ flags) {
+  const int kb = blockIdx.x, t = blockIdx.y;
+  const int pieces = k_pad / 8;  // 16-byte pieces per row
+  bool nz = false;
+  for (int q = threadIdx.x; q < bn * (kBK / 8); q += blockDim.x) {
+    const int r = t * bn + q / (kBK / 8);
+    if (r < n_rec) {
+      const size_t i = (size_t)r * pieces + (size_t)kb * (kBK / 8) + (q % (kBK / 8));
+      const uint4 a = hi[i], b = lo[i];
+      nz |= ((a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) & 0x7fff7fffu) != 0u;
     }
-  atomicMin(&first, f);
-  atomicMax(&last, l);
-  __syncthreads();
-  if (threadIdx.x == 0) out[blockIdx.x] = last < 0 ? make_int2(0, 1) : make_int2(first, last + 1);
+  }
+  nz = __syncthreads_or(nz);
+  if (threadIdx.x == 0) flags[(size_t)t * gridDim.x + kb] = nz ? 1 : 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -726,22 +725,45 @@ void tc_release(srw_ctx* h) {
   h->tmap = nullptr;
 }
 
+// K-block range {first, end} of each rec tile of width bn: the blocks of 64
+// true bins in which some row of the tile has a nonzero hi or lo element.
+// Outside the range every product is an exact zero, so the folds skip those
+// blocks without changing a bit of the accumulation.  A tile without any
+// nonzero element keeps one block (its accumulator must still be written).
 cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s) {
-  for (int f16 = 0; f16 < 2; ++f16)
-    for (int bi = 0; bi < 2; ++bi) {
+  const int n_kb = h->k_pad / kBK;
+  unsigned char* d_flags = nullptr;
+  const int max_tiles = (h->n_rec + 127) / 128;
+  cudaError_t e = cudaMalloc(&d_flags, (size_t)max_tiles * n_kb);
+  if (e != cudaSuccess) return e;
+  std::vector<unsigned char> flags((size_t)max_tiles * n_kb);
+  for (int f16 = 0; f16 < 2 && e == cudaSuccess; ++f16)
+    for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
       const int bn = bi ? 256 : 128, n_tiles = (h->n_rec + bn - 1) / bn;
-      cudaError_t e = cudaMalloc(&h->d_kbr[f16][bi], sizeof(int2) * n_tiles);
-      if (e != cudaSuccess) return e;
+      const uint4* hi = reinterpret_cast<const uint4*>(f16 ? (const void*)h->d_rhi16 : (const void*)h->d_rhi);
+      const uint4* lo = reinterpret_cast<const uint4*>(f16 ? (const void*)h->d_rlo16 : (const void*)h->d_rlo);
+      kb_flags_kernel<<<dim3(n_kb, n_tiles), 256, 0, s>>>(hi, lo, h->n_rec, h->k_pad, bn, d_flags);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = cudaMemcpyAsync(flags.data(), d_flags, (size_t)n_tiles * n_kb, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        break;
+      std::vector<int2>& r = h->kbr_h[f16][bi];
+      r.assign(n_tiles, make_int2(0, 1));
+      for (int t = 0; t < n_tiles; ++t) {
+        int first = -1, last = -1;
+        for (int kb = 0; kb < n_kb; ++kb)
+          if (flags[(size_t)t * n_kb + kb]) {
+            if (first < 0) first = kb;
+            last = kb;
+          }
+        if (first >= 0) r[t] = make_int2(first, last + 1);
+      }
+      if ((e = cudaMalloc(&h->d_kbr[f16][bi], sizeof(int2) * n_tiles)) != cudaSuccess) break;
       h->device_bytes += sizeof(int2) * n_tiles;
-      const unsigned short* hi = reinterpret_cast<const unsigned short*>(f16 ? (const void*)h->d_rhi16 : (const void*)h->d_rhi);
-      const unsigned short* lo = reinterpret_cast<const unsigned short*>(f16 ? (const void*)h->d_rlo16 : (const void*)h->d_rlo);
-      kb_range_kernel<<<n_tiles, 256, 0, s>>>(hi, lo, h->n_rec, h->k_pad, bn, h->d_kbr[f16][bi]);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      h->kbr_h[f16][bi].resize(n_tiles);
-      e = cudaMemcpyAsync(h->kbr_h[f16][bi].data(), h->d_kbr[f16][bi], sizeof(int2) * n_tiles, cudaMemcpyDeviceToHost, s);
-      if (e != cudaSuccess) return e;
+      e = cudaMemcpy(h->d_kbr[f16][bi], r.data(), sizeof(int2) * n_tiles, cudaMemcpyHostToDevice);
     }
-  return cudaStreamSynchronize(s);
+  cudaFree(d_flags);
+  return e;
 }
 
 double tc_block_fraction(const srw_ctx* h, int bn, bool f16) {
