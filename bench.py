@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import datetime
 import hashlib
 import io
 import json
@@ -41,7 +42,8 @@ WORKLOAD_DATA = "solar_set_4096"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 200; 20 for --impl reference, whose steps take seconds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srw", choices=["srw", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16x3", "bf16x3", "bf16", "fp32"])
@@ -60,7 +62,10 @@ def parse():
     ap.add_argument("--groups", type=int, default=64, help="configurations of the grouped workload")
     ap.add_argument("--group-scale", type=float, default=1.0,
                     help="size factor of the grouped workload (profiling captures of a smaller case)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 200
+    return args
 
 
 # tensor-core products per useful flop, and the peak each precision is held to
@@ -211,28 +216,43 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- clocks
 class Clocks:
-    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
-             "clocks_event_reasons.sw_power_cap"
+    """nvidia-smi samples (every 50 ms, timestamped) of the SM clock and the
+    throttle reasons; only the samples inside the timed window are kept."""
+    FIELDS = "timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling and wait (up to 10 s) for the first sample."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        deadline = time.time() + 10.0
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_stop(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.1)  # one more sample after the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -241,21 +261,27 @@ class Clocks:
         self.fh.close()
         rows = []
         for r in csv.reader(io.StringIO(open(self.path).read())):
-            if len(r) < 9:
+            if len(r) < 10:
                 continue
+            r = [x.strip() for x in r]
             try:
-                rows.append([x.strip() for x in r])
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
             except ValueError:
                 continue
-        if not rows:
+            rows.append((ts, r))
+        window = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
+        if not window:  # the window was shorter than the sampling period: the samples bracketing it
+            window = [r for ts, r in rows if self.t0 is not None and ts <= self.t1][-1:] + \
+                     [r for ts, r in rows if self.t1 is not None and ts > self.t1][:1]
+        if not window:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[2]) for r in window if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in window if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
-        load = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
-        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[k] for r in window for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(window),
+                "window_s": (self.t1 - self.t0).total_seconds() if self.t0 and self.t1 else None}
 
 
 # --------------------------------------------------------------------------- roofline inputs
@@ -512,6 +538,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     step_ms, fold_ms = [], []
     for _ in range(args.steps):
         flush.add_(1.0)
@@ -522,6 +549,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         fold_ms.append(srw.srw_profile_read(h))
     torch.cuda.synchronize()
+    clocks.mark_stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()

@@ -341,7 +341,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
       if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
       const int bn = GROUPED ? G.bn : BN, nt = n0 / bn, n_rec = G.n_rec, P = G.P;
-      const float2* nb2 = G.nb2;
+      const float4* nb4 = G.nb4;
       const int buf = tc & 1;
       if (!warp_wait(&acc_full[buf], (tc >> 1) & 1, &abort_flag, 256)) {
         give_up();
@@ -350,46 +350,51 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       tc_fence_after();
       const int p = m0 + q * 32 + lane;
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
-      const float* rinv = G.rinv;
       float sinv = 1.f;  // 1 / s_p (exact: s_p is a power of two)
       if (F16 && p < P) sinv = 1.f / L.wscale[(size_t)G.p_off + p];
       dfloat acc = {0.f, 0.f};
       bool infinite = false;  // a +inf term (mu <= 0 with data) is kept apart: TwoSum would make it NaN
+      float mneg = 0.f;       // smallest mu of the active bins (below 0: outside the domain)
 #pragma unroll 1
       for (int c0 = 0; c0 < bn; c0 += 16) {
         // per-column constants first (warp-uniform loads), then the accumulator row
-        float2 dj[16];
+        float4 dj[16];
         if (parts != nullptr) {
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int j = n0 + c0 + k;
-            dj[k] = j < n_rec ? __ldg(nb2 + j) : make_float2(-1.f, 1.f);  // n_j (-1: masked), b_j + ref
+            // {n_j (0 where masked), b_j + R W_ref, mask, 1/r_j}; padding columns add nothing
+            dj[k] = j < n_rec ? __ldg(nb4 + j) : make_float4(0.f, 1.f, 0.f, 0.f);
+          }
+        } else {  // folded spectra only (no data needed): just the row scales
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int j = n0 + c0 + k;
+            dj[k] = make_float4(0.f, 0.f, 0.f, F16 && j < n_rec ? __ldg(G.rinv + j) : 0.f);
           }
         }
-        float v[16], sj[16];
+        float v[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {  // the power-of-two scales of both operands (exact)
-          const int j = n0 + c0 + k;
-          sj[k] = F16 ? sinv * (j < n_rec ? __ldg(rinv + j) : 0.f) : 1.f;
-        }
         if (musig_out != nullptr && p < P) {  // batched folded spectra (row p)
           float* row = musig_out + (size_t)(G.p_off + p) * n_rec;
 #pragma unroll
           for (int k = 0; k < 16; ++k)
-            if (n0 + c0 + k < n_rec) row[n0 + c0 + k] = v[k] * sj[k];
+            if (n0 + c0 + k < n_rec) row[n0 + c0 + k] = F16 ? v[k] * (sinv * dj[k].w) : v[k];
         }
         if (parts != nullptr) {
           float ts = 0.f;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const float t = poisson_term_f32_sel(F16 ? fmaf(v[k], sj[k], dj[k].y) : v[k] + dj[k].y, dj[k].x);
-            ts += dj[k].x >= 0.f ? t : 0.f;  // masked and padding columns add nothing
+            // the power-of-two scales of both operands come out exactly
+            const float mu = F16 ? fmaf(v[k], sinv * dj[k].w, dj[k].y) : v[k] + dj[k].y;
+            ts = fmaf(poisson_term_f32_tc(mu, dj[k].x), dj[k].z, ts);
+            mneg = fminf(mneg, mu * dj[k].z);
           }
-          if (isinf(ts)) infinite = true;
+          if (isinf(ts) || isnan(ts)) infinite = true;
           else acc = df_add(acc, ts);
         }
       }
+      if (mneg < 0.f) infinite = true;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
@@ -780,7 +785,7 @@ TcGroup tc_group_of(const srw_ctx* h, int bn, bool f16) {
   G.kbr = h->d_kbr[f16 ? 1 : 0][bn == 256 ? 1 : 0];
   G.map_hi = G.map_lo = nullptr;
   G.shat_k8 = reinterpret_cast<const float4*>(h->d_shat_k8);
-  G.nb2 = reinterpret_cast<const float2*>(h->d_nb2);
+  G.nb4 = h->d_nb4;
   G.c_data = h->d_cdata;
   G.parts_off = 0;
   G.n_rec = h->n_rec;

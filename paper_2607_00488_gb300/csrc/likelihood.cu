@@ -212,7 +212,8 @@ __global__ void data_prepare_kernel(const double* __restrict__ bkg, int n_bkg, i
 // in FP64 (SIMT fold) and as floats with the count and the mask (tensor fold).
 __global__ void data_ref_kernel(const double* __restrict__ n64, const double* __restrict__ b64,
                                 const double* __restrict__ muref, const unsigned char* __restrict__ mask, int n_rec,
-                                double* __restrict__ bref64, float4* __restrict__ nbm, float2* __restrict__ nb2) {
+                                const float* __restrict__ rinv, double* __restrict__ bref64, float4* __restrict__ nbm,
+                                float2* __restrict__ nb2, float4* __restrict__ nb4) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_rec) return;
   const double br = b64[j] + muref[j];
@@ -220,6 +221,7 @@ __global__ void data_ref_kernel(const double* __restrict__ n64, const double* __
   const bool on = mask == nullptr || mask[j] != 0;
   nbm[j] = make_float4((float)n64[j], (float)br, on ? 1.f : 0.f, 0.f);
   nb2[j] = make_float2(on ? (float)n64[j] : -1.f, (float)br);
+  if (nb4) nb4[j] = make_float4(on ? (float)n64[j] : 0.f, (float)br, on ? 1.f : 0.f, rinv ? rinv[j] : 1.f);
 }
 
 // C = 2 sum_j M_j [n_j - n_j ln n_j + lnGamma(n_j + 1)], one block.
@@ -292,7 +294,7 @@ cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStre
 cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s) {
   const int thr = 256;
   data_ref_kernel<<<(h->n_rec + thr - 1) / thr, thr, 0, s>>>(h->d_n64, h->d_b64, h->d_muref64, h->d_mask, h->n_rec,
-                                                             h->d_bref64, h->d_nbm, h->d_nb2);
+                                                             h->d_rinv, h->d_bref64, h->d_nbm, h->d_nb2, h->d_nb4);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && h->d_lin) e = launch_linear_consts(h, s);
   return e;

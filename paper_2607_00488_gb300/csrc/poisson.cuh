@@ -61,4 +61,24 @@ __device__ __forceinline__ float poisson_term_f32_sel(float mu, float n) {
   return (mu < 0.f || (mu == 0.f && n > 0.f)) ? __int_as_float(0x7f800000) : t;
 }
 
+// The tensor-core epilogue's term, branch-free and without per-element special
+// cases.  The bin constants carry n = 0 for masked bins (their term is then
+// finite and the caller multiplies it by the 0/1 mask).  The log argument is
+// floored at 1e-30: for n = 0 the term is 0 * ln(1e-30) = 0, so t = mu
+// (mu = 0 included, where n / mu is NaN and the floor applies); mu = 0 with
+// n > 0 gives +inf through ln(inf).  mu < 0 is left to the caller (it tracks
+// the smallest mu of the active bins).  Elsewhere identical to
+// poisson_term_f32_sel.
+__device__ __forceinline__ float poisson_term_f32_tc(float mu, float n) {
+  const float d = n - mu, s = n + mu;
+  const float v = __fdividef(d, s);
+  const float v2 = v * v;
+  float p = fmaf(v2, 1.f / 9.f, 1.f / 7.f);
+  p = fmaf(v2, p, 1.f / 5.f);
+  p = fmaf(v2, p, 1.f / 3.f);
+  const float ts = fmaf(d, v, 2.f * n * v * v2 * p);
+  const float tl = (mu - n) + n * logf(fmaxf(__fdividef(n, mu), 1e-30f));
+  return fabsf(v) < 0.1f ? ts : tl;
+}
+
 }  // namespace srw

@@ -83,7 +83,7 @@ struct TcGroup {
   const CUtensorMap* map_hi;   // R hi / lo maps, box 64 K x bn rows (grouped launches; global memory)
   const CUtensorMap* map_lo;
   const float4* shat_k8;       // [k_pad][8] coefficient spectra, k-major
-  const float2* nb2;           // [n_rec] {n_j or -1 where masked, b_j + R W_ref}
+  const float4* nb4;           // [n_rec] {n_j (0 where masked), b_j + R W_ref, mask 1/0, 1/r_j (FP16 row scale)}
   const double* c_data;        // data constant of -2 ln L (device scalar)
   long long parts_off;         // partial sums of the group: parts + parts_off, [n_tiles][P]
   int n_rec, k_pad, P, p_off;  // p_off: first point of the group in the launch's theta / out
@@ -164,7 +164,8 @@ struct srw_ctx {
   double* d_n64 = nullptr;
   double* d_b64 = nullptr;
   float4* d_nbm = nullptr;
-  float2* d_nb2 = nullptr;     // {n_j or -1 where masked, b_j + R W_ref} (tensor-core epilogue)
+  float2* d_nb2 = nullptr;     // {n_j or -1 where masked, b_j + R W_ref} (surrogate epilogue)
+  float4* d_nb4 = nullptr;     // {n_j (0 where masked), b_j + R W_ref, mask 1/0, 1/r_j} (tensor-core epilogue)
   unsigned char* d_mask = nullptr;
   double* d_cdata = nullptr;
 
