@@ -97,6 +97,10 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
     }
   } else {
     // ---- consumers (no FP64 here: the chunk sums accumulate as double-floats)
+    // W may come from a grid this one depends on programmatically: wait for it
+    // (returns at once without such a dependency); the producer's R stream
+    // does not depend on it and is already running
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     dfloat lacc = {0.f, 0.f};
     for (int u = 0; u < n_units; ++u) {
       const int st = u % kGvStages;
@@ -275,6 +279,26 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
       h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
       mu_out, h->d_part, h->d_ticket, out, h->d_status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* out, cudaStream_t s) {
+  const size_t smem = gv_smem(h);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const double* muref = h->use_ref ? h->d_muref64 : nullptr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(fold_point_grid(h));
+  cfg.blockDim = dim3(kGvThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fold_point_kernel, (const float*)h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W,
+                            muref, (const double*)h->d_n64, (const double*)h->d_b64,
+                            (const unsigned char*)h->d_mask, (const double*)h->d_cdata, (float*)nullptr,
+                            (float*)nullptr, h->d_part, h->d_ticket, out, h->d_status);
 }
 
 cudaError_t launch_reduce_parts(const srw_ctx* h, const double* parts, int n_parts, int P, double* out,

@@ -350,6 +350,9 @@ __global__ void shat_kernel(const double* __restrict__ basis, const double* __re
 __global__ void weights_from_basis_kernel(const float* __restrict__ theta, dfloat sin2w, CoefRef cref,
                                           const float* __restrict__ shat, const float* __restrict__ shat_lo,
                                           int k_pad, float* __restrict__ W) {
+  // a fold launched as this kernel's programmatic dependent may start now: it
+  // streams R and waits for this grid's W before using it
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ float ch[kNB], cl[kNB];
   if (threadIdx.x < kNB) {
     const dfloat s = sin2w;

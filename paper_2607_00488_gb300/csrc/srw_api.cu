@@ -909,7 +909,10 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
       cudaError_t e = launch_weights_from_basis(h, th, h->d_W, cs);
       if (e != cudaSuccess) return e;
       if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o, cs, true)) != cudaSuccess) return e;
+      // with profiling the fold runs after the recorded event; otherwise it
+      // overlaps its R stream with the weights kernel (programmatic dependency)
+      e = h->profile ? launch_fold_point(h, h->d_W, nullptr, nullptr, o, cs, true) : launch_fold_point_after(h, h->d_W, o, cs);
+      if (e != cudaSuccess) return e;
       if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
       return cudaSuccess;
     });

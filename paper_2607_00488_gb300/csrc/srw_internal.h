@@ -239,6 +239,9 @@ void fold_point_init();
 int fold_simt_parts(int n_rec);
 cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out, float* mu_out, double* out,
                               cudaStream_t s, bool delta = false);
+// The single-point fold (delta mode) as a programmatic dependent of the
+// preceding kernel on s: it starts while that kernel runs and waits for W.
+cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* out, cudaStream_t s);
 cudaError_t launch_reduce_parts(const srw_ctx* h, const double* parts, int n_parts, int P, double* out,
                                 cudaStream_t s);
 
