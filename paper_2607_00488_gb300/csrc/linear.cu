@@ -74,7 +74,8 @@ __global__ void linear_consts_kernel(const double* __restrict__ M, const double*
   const bool on = mask == nullptr || mask[j] != 0;
   out[3 * j] = make_float4((float)m[0], (float)m[1], (float)m[2], (float)m[3]);
   out[3 * j + 1] = make_float4((float)m[4], (float)m[5], (float)m[6], (float)m[7]);
-  out[3 * j + 2] = make_float4((float)(n - base), (float)(n + base), on ? (float)n : -1.f, 0.f);
+  const double nn = on ? n : 0.0;  // masked bins: n = 0 keeps their (multiplied-out) term finite
+  out[3 * j + 2] = make_float4((float)(nn - base), (float)(nn + base), (float)nn, on ? 1.f : 0.f);
   outp[j] = make_float4((float)muref[j], (float)(base - muref[j]), on ? (float)n : -1.f, 0.f);
 }
 
@@ -114,6 +115,21 @@ __device__ __forceinline__ float deviance_ds(float d, float s, float n) {
   return (mu < 0.f || (mu == 0.f && n > 0.f)) ? __int_as_float(0x7f800000) : t;
 }
 
+// The evaluator's term from d = n - mu and s = n + mu, without per-element
+// special cases: the log argument is floored at 1e-30, so n = 0 gives t = mu
+// (also for mu = 0) and mu = 0 < n gives +inf; mu < 0 is left to the caller.
+__device__ __forceinline__ float deviance_fast(float d, float s, float n) {
+  const float mu = n - d;
+  const float v = __fdividef(d, s);
+  const float v2 = v * v;
+  float p = fmaf(v2, 1.f / 9.f, 1.f / 7.f);
+  p = fmaf(v2, p, 1.f / 5.f);
+  p = fmaf(v2, p, 1.f / 3.f);
+  const float ts = fmaf(d, v, 2.f * n * v * v2 * p);
+  const float tl = -d + n * logf(fmaxf(__fdividef(n, mu), 1e-30f));
+  return fabsf(v) < 0.1f ? ts : tl;
+}
+
 // Four lanes per point (adjacent lanes), each on every fourth bin; their sums
 // are combined with shuffles.
 template <bool GRAD>
@@ -130,6 +146,7 @@ linear_loglik_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefR
   if (on) deviations(theta + (size_t)p * 5, sin2w, cref, c, g);
   dfloat acc = {0.f, 0.f};
   bool infinite = false;
+  float mneg = 0.f;  // smallest mu of the active bins (below 0: outside the domain)
   float gb[kNB] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j0 = 0; j0 < n_rec; j0 += kLinChunk) {
     const int cnt = min(kLinChunk, n_rec - j0);
@@ -140,8 +157,7 @@ linear_loglik_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefR
     int n_acc = 0;
 #pragma unroll 4
     for (int j = quarter; j < cnt; j += 4) {
-      const float4 m0 = sc[3 * j], m1 = sc[3 * j + 1], q = sc[3 * j + 2];
-      const bool live = q.z >= 0.f;  // masked bins add nothing
+      const float4 m0 = sc[3 * j], m1 = sc[3 * j + 1], q = sc[3 * j + 2];  // q.w: 1, or 0 where masked
       float dl = m0.x * c[0];
       dl = fmaf(m0.y, c[1], dl);
       dl = fmaf(m0.z, c[2], dl);
@@ -151,10 +167,10 @@ linear_loglik_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefR
       dl = fmaf(m1.z, c[6], dl);
       dl = fmaf(m1.w, c[7], dl);
       const float d = q.x - dl, s = q.y + dl;
-      const float t = deviance_ds(d, s, q.z);
-      ts += live ? t : 0.f;
+      ts = fmaf(deviance_fast(d, s, q.z), q.w, ts);
+      mneg = fminf(mneg, (q.z - d) * q.w);
       if (GRAD) {
-        const float r = live ? 1.f - __fdividef(q.z, q.z - d) : 0.f;  // 1 - n / mu
+        const float r = q.w > 0.f ? 1.f - __fdividef(q.z, q.z - d) : 0.f;  // 1 - n / mu
         gb[0] = fmaf(m0.x, r, gb[0]);
         gb[1] = fmaf(m0.y, r, gb[1]);
         gb[2] = fmaf(m0.z, r, gb[2]);
@@ -173,6 +189,7 @@ linear_loglik_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefR
     if (isinf(ts)) infinite = true;
     else acc = df_add(acc, ts);
   }
+  if (mneg < 0.f) infinite = true;
   // combine the four lanes of each point
 #pragma unroll
   for (int o = 1; o <= 2; o <<= 1) {
