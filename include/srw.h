@@ -286,8 +286,10 @@ srw_status srw_info(srw_handle h, srw_info_t* info);
  * computed once in FP64, so the rounding errors of the FP32 and BF16 folds
  * scale with |W(theta) - W_ref| instead of |W(theta)|.  The default
  * reference is the SM point theta = 0.  theta_ref (5 floats, host memory)
- * selects another point (e.g. the current best fit); NULL disables the
- * reference (mu = R W(theta) folded directly in the chosen precision).
+ * selects another point (e.g. the current best fit); NULL removes the
+ * point: the folds then carry all of W(theta) in the chosen precision except
+ * its theta-independent part (the nu_mu spectrum), which is folded once in
+ * FP64 in every mode.
  * Synchronous; invalidates captured graphs. */
 srw_status srw_set_reference(srw_handle h, const float* theta_ref);
 

@@ -302,7 +302,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             for (int rr = 0; rr < 4; ++rr) {
               float a = c[rr][0] * sv[0];
 #pragma unroll
-              for (int bb = 1; bb < kNB; ++bb) a = fmaf(c[rr][bb], sv[bb], a);
+              for (int bb = 1; bb < kNB; ++bb)  // the constant monomial (6) is always in the reference fold
+                if (bb != 6) a = fmaf(c[rr][bb], sv[bb], a);
               w[rr][e] = a;
             }
           }

@@ -274,7 +274,7 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
                               cudaStream_t s, bool delta) {
   const size_t smem = gv_smem(h);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  const double* muref = (delta && h->use_ref) ? h->d_muref64 : nullptr;
+  const double* muref = delta ? h->d_muref64 : nullptr;
   fold_point_kernel<<<fold_point_grid(h), kGvThreads, smem, s>>>(
       h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
       mu_out, h->d_part, h->d_ticket, out, h->d_status);
@@ -284,7 +284,7 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
 cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* out, cudaStream_t s) {
   const size_t smem = gv_smem(h);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  const double* muref = h->use_ref ? h->d_muref64 : nullptr;
+  const double* muref = h->d_muref64;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(fold_point_grid(h));
   cfg.blockDim = dim3(kGvThreads);
@@ -332,7 +332,6 @@ __global__ void add_ref_kernel(float* __restrict__ out, const double* __restrict
 }
 
 cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s) {
-  if (!h->use_ref) return cudaSuccess;
   const size_t n = (size_t)P * h->n_rec;
   add_ref_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, h->d_muref64, P, h->n_rec);
   return cudaGetLastError();

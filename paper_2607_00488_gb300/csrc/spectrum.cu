@@ -422,7 +422,6 @@ __global__ void muref_kernel(const float* __restrict__ R, int ld, int n_t, const
 }  // namespace
 
 cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s) {
-  if (!h->use_ref) return cudaMemsetAsync(h->d_muref64, 0, sizeof(double) * h->n_rec, s);
   double* d_w = nullptr;
   cudaError_t e = cudaMallocAsync(&d_w, sizeof(double) * h->n_t, s);
   if (e != cudaSuccess) return e;

@@ -89,7 +89,11 @@ static void split_df(double x, float* hi, float* lo) {
 }
 
 // Monomials (batched folds) and coupling products (spectrum kernel) of the
-// reference point, in FP64 split into hi + lo floats; zeros when disabled.
+// reference point, in FP64 split into hi + lo floats.  Without a reference
+// point the monomials are those of the theta-independent term alone
+// (c = 1 for the nu_mu spectrum, 0 otherwise): it is folded once in FP64 and
+// the folds never carry it, so their constant-monomial coefficient is always
+// exactly zero.  The spectrum kernel's coupling products are zero then.
 static void set_reference_coefs(srw_ctx* h) {
   const double s = h->sin2w;
   const double* t = nullptr;
@@ -103,7 +107,10 @@ static void set_reference_coefs(srw_ctx* h) {
                         gle * gre, glm * grm, glt * grt, h->kappa * mu2};
   for (int b = 0; b < kNB; ++b) {
     if (h->use_ref) split_df(c[b], &h->cref.hi[b], &h->cref.lo[b]);
-    else h->cref.hi[b] = h->cref.lo[b] = 0.f;
+    else {
+      h->cref.hi[b] = b == 6 ? 1.f : 0.f;
+      h->cref.lo[b] = 0.f;
+    }
   }
   for (int k = 0; k < 10; ++k) {
     if (h->use_ref) split_df(g[k], &h->gref[0][k], &h->gref[1][k]);
@@ -856,8 +863,9 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
     // stage 1 returns the full W; stages 2 and 3 fold the deviation from the reference point
     float* Wbuf = (stage == 1 && dev) ? out : h->d_W;
     SRW_CUDA(h, launch_spectrum_point(h, th, nullptr, Wbuf, nullptr, s, stage >= 2), "spectrum kernel");
-    if (stage == 2) SRW_CUDA(h, launch_fold_point(h, h->d_W, dst, nullptr, nullptr, s, true), "fold kernel");
-    if (stage == 3) SRW_CUDA(h, launch_fold_point(h, h->d_W, nullptr, dst, nullptr, s, true), "fold kernel");
+    // the spectrum kernel forms a deviation only with a reference point set
+    if (stage == 2) SRW_CUDA(h, launch_fold_point(h, h->d_W, dst, nullptr, nullptr, s, h->use_ref != 0), "fold kernel");
+    if (stage == 3) SRW_CUDA(h, launch_fold_point(h, h->d_W, nullptr, dst, nullptr, s, h->use_ref != 0), "fold kernel");
   }
   if (!dev) {
     SRW_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(float) * n_out, cudaMemcpyDeviceToHost, s), "download");
@@ -899,7 +907,8 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
         cudaError_t e = h->joint ? launch_weights_from_basis(h, th + 5 * (size_t)p, h->d_W, cs)
                                  : launch_spectrum_point(h, th + 5 * (size_t)p, nullptr, h->d_W, nullptr, cs, true);
         if (e != cudaSuccess) return e;
-        if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o + p, cs, true)) != cudaSuccess) return e;
+        if ((e = launch_fold_point(h, h->d_W, nullptr, nullptr, o + p, cs, h->joint || h->use_ref)) != cudaSuccess)
+          return e;
       }
       return cudaSuccess;
     });

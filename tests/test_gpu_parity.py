@@ -220,9 +220,10 @@ def test_batched_spectra_per_bin(srw, solar, prec, tol):
 
 @pytest.mark.parametrize("prec,tol", [("bf16", TOL_BF16_BIN), ("fp16x3", TOL_FP16X3_BIN)])
 def test_raw_fold_without_reference(srw, solar, prec, tol):
-    # the reference point switched off: the whole W(theta) goes through the
-    # rounded operands (BF16: every product rounded to 8 bits; FP16 split:
-    # scaled to the largest element of W, not of a small deviation)
+    # the reference point removed: all of W(theta) but its theta-independent
+    # (nu_mu) part goes through the rounded operands (BF16: every product
+    # rounded to 8 bits; FP16 split: scaled to the largest element of W, not
+    # of a small deviation)
     th = workloads.theta_box(3, 14)
     try:
         solar.lk.set_reference(None)
