@@ -8,16 +8,18 @@
 //
 //   warps 0-7  W producers: each thread owns four points (rows) of the
 //              128-row A tile and 8 of the 64 K of the current block (warp w
-//              takes K chunk w); it computes W from the coefficients and the
-//              block's coefficient spectra (streamed into a shared-memory ring,
-//              read as warp-uniform loads), splits W into BF16 hi (+ lo) and
-//              writes it in the 128-byte-swizzled K-major layout the tensor
-//              core reads.
+//              takes K chunk w); it computes W from the coefficients (seven
+//              terms: the constant monomial is always in the reference fold)
+//              and the block's coefficient spectra (streamed into a
+//              shared-memory ring, read as warp-uniform loads), splits W into
+//              hi (+ lo) halves and writes it in the 128-byte-swizzled K-major
+//              layout the tensor core reads.
 //   warps 8-11 epilogue: thread = point; reads its accumulator row from
 //              tensor memory (TMEM lane = point, column = rec bin), adds the
-//              background, applies the mask, evaluates the Poisson terms and
-//              accumulates them per point (double-float), one FP64 partial per
-//              (rec tile, point).
+//              background and reference fold (one float4 of constants per
+//              bin), evaluates the Poisson terms with the mask multiplied out
+//              and accumulates them per point (double-float), one FP64 partial
+//              per (rec tile, point).
 //   warp 12    TMA producers: lane 0 streams R hi (+ lo) tiles, 64 x BN,
 //              128-byte swizzle; lane 1 streams the 2 KB coefficient-spectra
 //              slice of each K block, up to kShatSlots blocks ahead.
@@ -34,6 +36,10 @@
 // full precision from 2^-14 up to 65504); the epilogue multiplies the
 // accumulator by 1 / (s_p r_j), which is exact.  The accumulator is double-buffered
 // (2 x BN columns) so the epilogue of one tile overlaps the next tile's MMAs.
+//
+// Each rec tile runs only the range of K blocks in which its split response
+// has nonzero elements (kbr, from create time); the skipped blocks hold
+// zeros in both halves, so their products are exact zeros.
 //
 // Grouped launches (several detector configurations with their own binning,
 // response, data and points in one persistent grid) use the same kernel: each
