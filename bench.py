@@ -27,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -225,13 +226,13 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        fd, self.path = tempfile.mkstemp(prefix="srw_clocks_", suffix=".csv")
+        os.close(fd)
         self.t0 = self.t1 = None
 
     def start(self):
         """Start sampling and wait (up to 10 s) for the first sample."""
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -269,6 +270,10 @@ class Clocks:
             except ValueError:
                 continue
             rows.append((ts, r))
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         window = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
         if not window:  # the window was shorter than the sampling period: the samples bracketing it
             window = [r for ts, r in rows if self.t0 is not None and ts <= self.t1][-1:] + \

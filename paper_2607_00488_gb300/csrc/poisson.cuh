@@ -41,7 +41,7 @@ __device__ __forceinline__ float poisson_term_f32_tc(float mu, float n) {
   p = fmaf(v2, p, 1.f / 5.f);
   p = fmaf(v2, p, 1.f / 3.f);
   const float ts = fmaf(d, v, 2.f * n * v * v2 * p);
-  const float tl = (mu - n) + n * logf(fmaxf(__fdividef(n, mu), 1e-30f));
+  const float tl = fmaf(n, logf(fmaxf(__fdividef(n, mu), 1e-30f)), -d);  // mu - n = -d exactly
   return fabsf(v) < 0.1f ? ts : tl;
 }
 
