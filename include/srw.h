@@ -383,7 +383,7 @@ srw_status srw_group_destroy(srw_group g);
  * Learned surrogate (the paper has no counterpart; it serves dense scans):
  * a GELU MLP theta -> log mu_j (expected counts per reconstructed bin of
  * handle h), widths 5 -> 256 -> 256 -> 256 -> n_rec, trained on spectra of
- * the exact path and used to pre-screen scans, with the exact path as judge.
+ * the exact path and used to pre-screen scans, with the exact path deciding.
  *   x = (theta - centre) / half_width;  h_k = gelu(W_k h_{k-1} + b_k)  (k = 1..3,
  *   gelu(z) = z Phi(z));  y = W_4 h_3 + b_4;  log mu_j = m_j + s_j y_j
  * with per-bin standardization (m_j, s_j) of the training targets (identity
