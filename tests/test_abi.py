@@ -112,3 +112,26 @@ def test_create_joint_rejects_invalid_arguments(srw, bad):
     with pytest.raises(srw.SrwError) as ei:
         srw.srw_create_joint(t, comps, hist, expo, **a)
     assert ei.value.status == 1  # SRW_EINVAL, raised before any device call
+
+
+def test_missing_library_fails_loudly(srw, monkeypatch):
+    # the binding has no fallback: without the built library every call raises
+    from paper_2607_00488_gb300 import srw as binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libsrw.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.lib()
+    a = _args()
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.srw_create(a["t_edges"], a["n_rec"], a["sources"], a["R"], a["exposure"])
+
+
+def test_valid_create_without_a_device_fails_loudly(srw):
+    # valid arguments and no usable sm_103 device: an error status, never a CPU path
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    a = _args()
+    with pytest.raises(srw.SrwError) as ei:
+        srw.srw_create(a["t_edges"], a["n_rec"], a["sources"], a["R"], a["exposure"])
+    assert ei.value.status in (3, 7)  # SRW_ECUDA, SRW_EUNSUPPORTED
