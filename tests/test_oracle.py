@@ -195,6 +195,18 @@ def test_spectrum_is_linear_in_coupling_monomials(solar_workload):
         np.testing.assert_allclose(O.coupling_coefficients(th, wl["sin2w"]) @ b, s, rtol=1e-12, atol=1e-15 * s.max())
 
 
+def test_midpoint_spectrum_is_linear_in_coupling_monomials(solar_workload):
+    # the same decomposition holds bin by bin in the midpoint mode (eq. fT literally)
+    wl = solar_workload
+    edges = wl["t_edges"][::8]  # 512 bins: every source still spans many of them
+    b = O.coefficient_spectra(wl["sources"], edges, wl["t_min"], wl["sin2w"], wl["f_tau"], midpoint=True)
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        th = np.concatenate([rng.uniform(-0.3, 0.3, 4), rng.uniform(0, 3, 1)])
+        s = O.recoil_spectrum(wl["sources"], edges, th, wl["t_min"], wl["sin2w"], wl["f_tau"], midpoint=True)
+        np.testing.assert_allclose(O.coupling_coefficients(th, wl["sin2w"]) @ b, s, rtol=1e-12, atol=1e-15 * s.max())
+
+
 def test_magnetic_moment_only_adds(be7_workload):
     wl = be7_workload
     s0 = O.recoil_spectrum(wl["sources"], wl["t_edges"], np.zeros(5), wl["t_min"])
