@@ -113,17 +113,14 @@ def workload_config(P, precision, extra=None):
 def fit_region_points(n, seed=99):
     """Points near the SM reference (|eps| <= 0.02, mu_hat <= 0.5): where a fit
     or a confidence interval on this data is decided."""
-    import numpy as np
-    rng = np.random.default_rng(seed)
-    th = np.zeros((n, 5), np.float32)
-    th[:, :4] = rng.uniform(-0.02, 0.02, (n, 4))
-    th[:, 4] = rng.uniform(0.0, 0.5, n)
-    return th
+    import workloads
+    return workloads.fit_region_points(n, seed)
 
 
 def _oracle_sample(P, n, seed, n_fit=0):
-    """Run the FP64 oracle on n points of the workload (and n_fit fit-region
-    points) in this process; the timing covers the batch points only."""
+    """Run the FP64 oracle on n evenly spaced points of the workload (timed) and
+    on n_fit fit-region points; return with them the expected counts and the
+    folded signal of the n points (for the per-bin error budget)."""
     import numpy as np
 
     import workloads
@@ -137,7 +134,26 @@ def _oracle_sample(P, n, seed, n_fit=0):
     vals = model.neg2lnl_batch(wl["theta"][idx].astype(np.float64))
     dt = time.perf_counter() - t0
     fit = model.neg2lnl_batch(fit_region_points(n_fit).astype(np.float64)) if n_fit else np.zeros(0)
-    return idx.tolist(), vals.tolist(), dt, fit.tolist()
+    mus = [model.mu(t).tolist() for t in wl["theta"][idx].astype(np.float64)]
+    sigs = [model.mu_sig(t).tolist() for t in wl["theta"][idx].astype(np.float64)]
+    return idx.tolist(), vals.tolist(), dt, fit.tolist(), mus, sigs
+
+
+def parity_block(bar, region, fit_d, box_d, budgets, per_path):
+    """The parity claim of the line: the metric's bar holds in the fit region
+    (points within about Delta(-2 ln L) = 200 of the 1e5-event data, where fits
+    and intervals are decided); far from the data (the box sample) the bar
+    does not apply and each point is held to |d| <= bar + 2 B with the measured
+    per-bin budget B = 2 sum_j |1 - n_j/mu_j| |dmu_j|."""
+    fit_d = [float(x) for x in fit_d]
+    box_d = [float(x) for x in box_d]
+    budgets = [float(x) for x in budgets]
+    within = [d <= bar + 2.0 * b for d, b in zip(box_d, budgets)]
+    return {"bar": bar, "region": region,
+            "fit_region_n": len(fit_d), "fit_region_max_abs_d": max(fit_d), "fit_region_pass": bool(max(fit_d) <= bar),
+            "box_sample_n": len(box_d), "box_sample_max_abs_d": max(box_d),
+            "box_sample_median_abs_d": statistics.median(box_d), "box_sample_max_budget_B": max(budgets),
+            "box_sample_within_bar_plus_2B": bool(all(within)), "fit_region_max_abs_d_by_path": per_path}
 
 
 def _oracle_share(P, n, seed, part, parts):
@@ -363,17 +379,19 @@ def grouped_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, p
         fold_ms.append(grp.profile_read())
     grp.profile(False)
     fold_s = statistics.mean(fold_ms) * 1e-3
-    peak = peaks["bf16_tflops"] / PRODUCTS[prec]
+    peak = peaks["bf16_tflops"]
     n_pts = int(th.shape[0])
     res = {
         "workload": gw["name"], "configurations": len(P), "points": n_pts,
         "evals_s": n_pts * args.steps / (sum(step_ms) * 1e-3), "ms_per_step": statistics.mean(step_ms),
         "launches_per_step": 3 if prec == srw.SRW_FP16X3 else 2,
-        "roofline": {"bound": "tensor", "achieved": useful / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": useful / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel (grouped)",
-                     "useful_tflop_per_launch": useful / 1e12, "fold_ms": statistics.mean(fold_ms),
-                     "executed_block_fraction": useful / dense, "dense_equivalent_tflops": dense / fold_s / 1e12,
-                     "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec])},
+        "roofline": {"bound": "tensor", "achieved": dense / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": dense / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel (grouped)",
+                     "flops_definition": "useful: sum over configurations of 2 N_rec N_T P",
+                     "useful_tflop_per_launch": dense / 1e12, "fold_ms": statistics.mean(fold_ms),
+                     "frac_executed": useful * PRODUCTS[prec] / fold_s / 1e12 / peak,
+                     "executed_block_fraction": useful / dense,
+                     "peak_source": "%s bf16 dense burst" % peak_src},
         "schedule": {"candidate": cand, "bn_max": sched["bn_max"], "items": sched["n_items"], "ctas": sched["n_cta"],
                      "configs_bn128": sum(1 for b in sched["bn"] if b == 128)},
     }
@@ -396,34 +414,31 @@ def joint_measurement(args, srw, workloads, dev, stream, flush, prec, peaks, pea
     srw.srw_autotune(lk.handle, args.points, prec)
     th = torch.tensor(wl["theta"], device=dev)
     out = torch.empty(args.points, dtype=torch.float64, device=dev)
-    srw.srw_profile(lk.handle, True)
+    call = lambda: lk.loglik(th, prec, out=out, stream=stream)  # noqa: E731
     for _ in range(args.warmup):
         flush.add_(1.0)
-        lk.loglik(th, prec, out=out, stream=stream)
+        call()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    step_ms, fold_ms = [], []
-    for _ in range(args.steps):
-        flush.add_(1.0)
-        e0.record(stream)
-        lk.loglik(th, prec, out=out, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        fold_ms.append(srw.srw_profile_read(lk.handle))
-    srw.srw_profile(lk.handle, False)
+    step_ms = timed_steps(call, flush, stream, args.steps)
+    fold_ms = fold_kernel_ms(srw, lk.handle, call, flush, args.steps)
     work = lk.fold_work(prec)
     dense = 2.0 * info["n_rec"] * info["n_t"] * args.points
     fold_s = statistics.mean(fold_ms) * 1e-3
-    peak = peaks["bf16_tflops"] / PRODUCTS[prec]
+    peak = peaks["bf16_tflops"]
     res = {"workload": "solar joint response, 6 components x 1e7 MC events, 4096 x 2048 bins",
            "fold_axis": info["n_t"], "points": args.points,
            "evals_s": args.points * args.steps / (sum(step_ms) * 1e-3), "ms_per_step": statistics.mean(step_ms),
-           "roofline": {"bound": "tensor", "achieved": dense * work / fold_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "frac": dense * work / fold_s / 1e12 / peak, "kernel": "fold_tc_kernel",
+           # the concatenated axis is 79 % exact-zero blocks (each component's band),
+           # so its dense-equivalent rate says little: the executed tensor-core work
+           # (three products on the nonzero blocks) is held to the peak
+           "roofline": {"bound": "tensor", "achieved": dense * work * PRODUCTS[prec] / fold_s / 1e12, "peak": peak,
+                        "unit": "TFLOP/s", "frac": dense * work * PRODUCTS[prec] / fold_s / 1e12 / peak,
+                        "kernel": "fold_tc_kernel",
+                        "flops_definition": "executed: %d products x 2 N_rec K per point on the nonzero blocks"
+                                            % PRODUCTS[prec],
+                        "dense_equivalent_tflops": dense / fold_s / 1e12,
                         "executed_block_fraction": work, "fold_ms": statistics.mean(fold_ms),
-                        "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec])}}
+                        "peak_source": "%s bf16 dense burst" % peak_src}}
     lk.close()
     return res
 
@@ -475,6 +490,87 @@ def surrogate_measurement(args, srw, workloads, lk, peaks, peak_src):
                      "frac": achieved / peaks["bf16_tflops"], "kernel": "mlp_gemm_kernel (surrogate pass)",
                      "flop_per_point": flop_point, "peak_source": "%s (bf16 burst)" % peak_src},
     }
+
+
+
+def _plain(x):
+    """numpy scalars and arrays in the JSON line as plain numbers and lists."""
+    if hasattr(x, "tolist"):
+        return x.tolist()
+    if hasattr(x, "item"):
+        return x.item()
+    raise TypeError(type(x).__name__)
+
+
+# --------------------------------------------------------------------------- step timing
+def timed_steps(call, flush, stream, steps):
+    """`steps` calls, each after an L2 flush, timed with CUDA events on `stream`."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.add_(1.0)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def fold_kernel_ms(srw, h, call, flush, steps):
+    """Device time of the fold kernel alone, per step: the library's profiling
+    mode launches the step's kernels directly with CUDA events around the fold
+    launch (what ncu's gpu__time_duration measures), L2 flushed before each."""
+    srw.srw_profile(h, True)
+    try:
+        call()
+        ms = []
+        for _ in range(steps):
+            flush.add_(1.0)
+            call()
+            ms.append(srw.srw_profile_read(h))
+    finally:
+        srw.srw_profile(h, False)
+    return ms
+
+
+def fold_roofline(srw, lk, info, prec, prec_name, P, fold_ms, peaks, peak_src):
+    """Roofline of the batched fold: useful flops 2 N_rec N_T per point (the
+    dense contraction, whatever the kernel skips or repeats) over the kernel's
+    own device time, against the measured burst peak; beside it the executed
+    tensor-core work (products x executed (rec tile, K block) pairs)."""
+    fold_s = statistics.mean(fold_ms) * 1e-3
+    work = lk.fold_work(prec)
+    dense = 2.0 * info["n_rec"] * info["n_t"] * P
+    if prec == srw.SRW_FP32:
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, kernel_file, tag = "alu", "paper_2607_00488_gb300/csrc/fold_simt.cu", "fold_simt_kernel"
+        note = "%s: %s" % (peak_src, PEAK_NOTE[prec])
+    else:
+        peak = peaks["bf16_tflops"]
+        bound, kernel_file, tag = "tensor", "paper_2607_00488_gb300/csrc/fold_tc.cu", "fold_tc_kernel"
+        note = "%s bf16 dense burst (fp16 runs at the same rate)" % peak_src
+    achieved = dense / fold_s / 1e12
+    executed = dense * work * PRODUCTS[prec]
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(kernel_file, tag + ":" + prec_name), "kernel": tag, "peak_source": note,
+            "flops_per_launch": dense, "flops_definition": "useful: 2 N_rec N_T per point",
+            "fold_ms": statistics.mean(fold_ms), "fold_ms_sd": statistics.pstdev(fold_ms),
+            "executed_tflops": executed / fold_s / 1e12, "frac_executed": executed / fold_s / 1e12 / peak,
+            "executed_block_fraction": work, "products_per_useful_flop": PRODUCTS[prec]}
+
+
+def autotune_record(srw, h, prec):
+    """The fold configuration in use for `prec` (chosen by srw_autotune) and how
+    many candidates the autotuner timed."""
+    if prec == srw.SRW_FP32:
+        return None
+    index, timed = srw.srw_get_fold_config(h, prec)
+    tile, k_block, stages = srw.srw_fold_config(index)
+    return {"config": index, "tile": tile, "k_block": k_block, "stages": stages, "candidates_timed": timed,
+            "candidates": len(srw.srw_fold_configs())}
 
 
 # --------------------------------------------------------------------------- main arm
@@ -530,29 +626,20 @@ def main():
     th = torch.tensor(wl["theta"], device=dev)
     out = torch.empty(P, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
-    srw.srw_profile(h, True)
+    call = lambda: lk.loglik(th, prec, out=out, stream=stream)  # noqa: E731
     for _ in range(args.warmup):
         flush.add_(1.0)
-        lk.loglik(th, prec, out=out, stream=stream)
+        call()
     torch.cuda.synchronize()
 
+    # the timed region: graph replays of the whole step, L2 flushed before each
     clocks = Clocks(local)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.mark_start()
-    step_ms, fold_ms = [], []
-    for _ in range(args.steps):
-        flush.add_(1.0)
-        e0.record(stream)
-        lk.loglik(th, prec, out=out, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        fold_ms.append(srw.srw_profile_read(h))
+    step_ms = timed_steps(call, flush, stream, args.steps)
     torch.cuda.synchronize()
     clocks.mark_stop()
     if dist:
@@ -560,33 +647,12 @@ def main():
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), dist)
     value = whole_job_value(world, args.steps, P, total_ms)
-    srw.srw_profile(h, False)
 
-    # roofline of the fold kernel (useful flops 2 N_rec N_T per point)
+    # the fold kernel alone (events around its launch, same flushed steps)
+    fold_ms = fold_kernel_ms(srw, h, call, flush, args.steps)
     peaks, peak_src = measured_peaks()
-    fold_avg_s = statistics.mean(fold_ms) * 1e-3
-    # useful flops 2 N_rec N_T per point on the (rec tile, K block) pairs the
-    # fold executes: blocks where the split response is all zero are skipped
-    work = lk.fold_work(prec)
-    dense = 2.0 * info["n_rec"] * info["n_t"] * P
-    useful = dense * work
-    if prec == srw.SRW_FP32:
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, kernel_file, tag = "alu", "paper_2607_00488_gb300/csrc/fold_simt.cu", "fold_simt_kernel"
-    else:
-        # useful flops against the effective peak of the precision: one
-        # tensor-core product per useful flop (bf16), three for the hi+lo
-        # splits (bf16x3, fp16x3; dense FP16 and BF16 run at the same rate)
-        peak = peaks["bf16_tflops"] / PRODUCTS[prec]
-        bound, kernel_file, tag = "tensor", "paper_2607_00488_gb300/csrc/fold_tc.cu", "fold_tc_kernel"
-    achieved = useful / fold_avg_s / 1e12
-    executed = useful * PRODUCTS[prec]
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(kernel_file, tag + ":" + prec_name),
-                "kernel": tag,
-                "peak_source": "%s (%s)" % (peak_src, PEAK_NOTE[prec]),
-                "executed_tflops": executed / fold_avg_s / 1e12, "fold_ms": statistics.mean(fold_ms),
-                "executed_block_fraction": work, "dense_equivalent_tflops": dense / fold_avg_s / 1e12}
+    roofline = fold_roofline(srw, lk, info, prec, prec_name, P, fold_ms, peaks, peak_src)
+    roofline["autotune"] = autotune_record(srw, h, prec)
 
     # the other tensor-core split timed the same way (reported beside the headline)
     alt = {}
@@ -594,26 +660,21 @@ def main():
     if alt_prec is not None:
         srw.srw_autotune(h, P, alt_prec)
         out_alt = torch.empty(P, dtype=torch.float64, device=dev)
-        srw.srw_profile(h, True)
+        call_alt = lambda: lk.loglik(th, alt_prec, out=out_alt, stream=stream)  # noqa: E731
         for _ in range(args.warmup):
             flush.add_(1.0)
-            lk.loglik(th, alt_prec, out=out_alt, stream=stream)
-        a_ms, a_fold = [], []
-        for _ in range(args.steps):
-            flush.add_(1.0)
-            e0.record(stream)
-            lk.loglik(th, alt_prec, out=out_alt, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            a_ms.append(e0.elapsed_time(e1))
-            a_fold.append(srw.srw_profile_read(h))
-        srw.srw_profile(h, False)
-        a_fold_s = statistics.mean(a_fold) * 1e-3
+            call_alt()
+        a_ms = timed_steps(call_alt, flush, stream, args.steps)
+        a_fold = fold_kernel_ms(srw, h, call_alt, flush, args.steps)
         alt_name = {v: k for k, v in srw.PRECISIONS.items()}[alt_prec]
+        a_roof = fold_roofline(srw, lk, info, alt_prec, alt_name, P, a_fold, peaks, peak_src)
         alt = {"precision": alt_name, "value": P * args.steps / (sum(a_ms) * 1e-3), "ms_per_step": statistics.mean(a_ms),
-               "fold_ms": statistics.mean(a_fold),
-               "executed_block_fraction": lk.fold_work(alt_prec),
-               "frac": dense * lk.fold_work(alt_prec) / a_fold_s / 1e12 / (peaks["bf16_tflops"] / PRODUCTS[alt_prec])}
+               "fold_ms": a_roof["fold_ms"], "frac": a_roof["frac"], "frac_executed": a_roof["frac_executed"],
+               "executed_block_fraction": a_roof["executed_block_fraction"],
+               "autotune": autotune_record(srw, h, alt_prec)}
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
 
     # the exact rank-8 evaluator on the same batch (disclosed beside the fold;
     # same -2 ln L, no contraction over the true bins)
@@ -650,23 +711,47 @@ def main():
            "d2h_bytes_per_step": P * 8}
 
     # single-point FP32 paths (the 50x denominator), one evaluation per call:
-    #  loglik_cold: srw_loglik with one point, L2 flushed before every call;
+    #  cold: srw_loglik with one point, L2 flushed before every call;
+    #  warm: the same call back to back (R, 33.5 MB, stays in the 129 MB L2, as
+    #  inside a fit loop);
+    #  paper protocol: 10 consecutive calls, the first dropped, mean +- sd of the
+    #  other 9 (the paper's Table timing);
+    #  gemv: the fold kernel alone, cold, and its HBM roofline (R read once);
     #  plain_points: the paper-style pipeline (cross-section integrals recomputed
     #  over all node/bin pairs, then the fold), 256 points back to back.
     single = {}
     th1 = torch.tensor(wl["theta"][:1], device=dev)
     o1 = torch.empty(1, dtype=torch.float64, device=dev)
-    lk.loglik(th1, srw.SRW_FP32, out=o1, stream=stream)
-    ms1 = []
-    for k in range(50):
-        flush.add_(1.0)
-        th1.copy_(th[k:k + 1])
+    one = lambda: lk.loglik(th1, srw.SRW_FP32, out=o1, stream=stream)  # noqa: E731
+    one()
+    ms_cold = timed_steps(one, flush, stream, 50)
+    single["loglik_cold_evals_s"] = 1e3 / statistics.mean(ms_cold)
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(200):  # queued back to back: R stays in L2, launches overlap execution
+        one()
+    e1.record(stream)
+    e1.synchronize()
+    single["loglik_warm_evals_s"] = 200e3 / e0.elapsed_time(e1)
+    proto = []
+    flush.add_(1.0)
+    for _ in range(10):
         e0.record(stream)
-        lk.loglik(th1, srw.SRW_FP32, out=o1, stream=stream)
+        one()
         e1.record(stream)
         e1.synchronize()
-        ms1.append(e0.elapsed_time(e1))
-    single["loglik_cold_evals_s"] = 1e3 / statistics.mean(ms1)
+        proto.append(e0.elapsed_time(e1))
+    single["paper_protocol_ms"] = {"mean": statistics.mean(proto[1:]), "sd": statistics.stdev(proto[1:]),
+                                   "calls": 10, "dropped": 1}
+    gemv_ms = fold_kernel_ms(srw, h, one, flush, 50)
+    r_bytes = 4.0 * info["n_rec"] * info["n_t"]
+    gemv_gbs = r_bytes / (statistics.mean(gemv_ms) * 1e-3) / 1e9
+    single["gemv"] = {"bound": "hbm", "kernel": "fold_point_kernel", "ms": statistics.mean(gemv_ms),
+                      "achieved": gemv_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gemv_gbs / peaks["hbm_gbs"],
+                      "bytes_definition": "R once, 4 N_rec N_T bytes (%.1f MB), L2 flushed" % (r_bytes / 1e6),
+                      "peak_source": "%s hbm copy" % peak_src}
     thb = th[:256].contiguous()
     ob = torch.empty(256, dtype=torch.float64, device=dev)
     lk.loglik_points(thb, out=ob, stream=stream)
@@ -679,9 +764,17 @@ def main():
     single["batched_over_single"] = value / world / single["loglik_cold_evals_s"]
     gpu_vals = out.cpu().numpy()
     n_fit = 8
-    gpu_fit = lk.loglik(fit_region_points(n_fit), prec)
-    alt_fit = lk.loglik(fit_region_points(n_fit), alt_prec) if alt else None
-    lin_fit = lk.loglik_linear(fit_region_points(n_fit))
+    fit_th = fit_region_points(n_fit)
+    fit_gpu = {prec_name: lk.loglik(fit_th, prec),
+               "fp32_batched": lk.loglik(fit_th, srw.SRW_FP32),
+               "fp32_single": np.array([lk.loglik(t[None, :], srw.SRW_FP32)[0] for t in fit_th]),
+               "rank8": lk.loglik_linear(fit_th)}
+    if alt:
+        fit_gpu[alt["precision"]] = lk.loglik(fit_th, alt_prec)
+    box_idx = np.linspace(0, P - 1, args.cpu_sample).astype(int)
+    box_sig = {prec_name: lk.spectrum_batch(wl["theta"][box_idx], prec)}
+    if alt:
+        box_sig[alt["precision"]] = lk.spectrum_batch(wl["theta"][box_idx], alt_prec)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -699,9 +792,7 @@ def main():
     if world == 1 and not args.no_surrogate and info["tensor_path"]:
         line["surrogate"] = surrogate_measurement(args, srw, workloads, lk, peaks, peak_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        idx, vals, dt, fit = oracle_subprocess(P, args.cpu_sample, 3, n_fit)
-        d = [abs(gpu_vals[i] - v) for i, v in zip(idx, vals)]
-        dfit = [abs(g - v) for g, v in zip(gpu_fit, fit)]
+        idx, vals, dt, fit, mus, sigs = oracle_subprocess(P, args.cpu_sample, 3, n_fit)
         line["cpu_baseline"] = {"value": len(idx) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "%d evenly spaced theta of the %d-point batch, FP64 numpy, 1 thread"
                                           % (len(idx), P)}
@@ -709,17 +800,37 @@ def main():
         line["cpu_baseline_all_cores"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                           "sample": "%d evenly spaced theta of the batch, one single-threaded process "
                                                     "per core" % (2 * cores)}
+        fit = np.asarray(fit)
+        per_path = {k: float(np.max(np.abs(np.asarray(v) - fit))) for k, v in fit_gpu.items()}
+        n = np.asarray(counts, np.float64)
+
+        def budgets(sig_gpu):
+            out_b = []
+            for k in range(len(idx)):
+                mu = np.asarray(mus[k])
+                dmu = np.asarray(sig_gpu[k], np.float64) - np.asarray(sigs[k])
+                on = mu > 0
+                out_b.append(float(2.0 * np.sum(np.abs(1.0 - n[on] / mu[on]) * np.abs(dmu[on]))))
+            return out_b
+        region = ("fit region: |eps| <= 0.02, mu_hat <= 0.5 around the SM reference point (1e5-event data, "
+                  "within about Delta(-2lnL) = 220 of it); the bar of the metric applies there")
+        bar = 1e-4 if prec == srw.SRW_FP32 else 1e-3
+        box_d = [abs(gpu_vals[i] - v) for i, v in zip(idx, vals)]
+        line["parity"] = parity_block(bar, region, [abs(g - v) for g, v in zip(fit_gpu[prec_name], fit)], box_d,
+                                      budgets(box_sig[prec_name]), per_path)
+        line["config"]["parity_region"] = region
         if alt:
-            alt["fit_region_max_abs_d"] = max(abs(g - v) for g, v in zip(alt_fit, fit))
-        lin["fit_region_max_abs_d"] = max(abs(g - v) for g, v in zip(lin_fit, fit))
-        line["parity"] = {"fit_region_n": len(dfit), "fit_region_max_abs_d": max(dfit),
-                          "box_sample_n": len(d), "box_sample_max_abs_d": max(d),
-                          "box_sample_median_abs_d": statistics.median(d)}
+            alt_vals = lk.loglik(wl["theta"][box_idx], alt_prec)
+            alt["parity"] = parity_block(1e-3, region, [abs(g - v) for g, v in zip(fit_gpu[alt["precision"]], fit)],
+                                         [abs(g - v) for g, v in zip(alt_vals, vals)],
+                                         budgets(box_sig[alt["precision"]]), None)
+            alt["fit_region_max_abs_d"] = alt["parity"]["fit_region_max_abs_d"]
+        lin["fit_region_max_abs_d"] = per_path["rank8"]
     if alt:
         line["other_split"] = alt
     line["rank8_evaluator"] = lin
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, default=_plain))
     lk.close()
     if dist:
         dist.destroy_process_group()

@@ -60,7 +60,8 @@ typedef enum {
   SRW_ENODATA = 4,      /* srw_loglik before srw_set_data */
   SRW_EDOMAIN = 5,      /* some mu_j <= 0 with n_j > 0 (or mu_j < 0): that point's -2lnL is +inf */
   SRW_ETIMEOUT = 6,     /* a bounded device-side wait expired; the kernel aborted cleanly */
-  SRW_EUNSUPPORTED = 7  /* the device cannot run the requested path (needs sm_103) */
+  SRW_EUNSUPPORTED = 7, /* the device cannot run the requested path (needs sm_103) */
+  SRW_ECHECK = 8        /* debug build only: an index bounds check or a buffer canary failed */
 } srw_status;
 
 typedef enum { SRW_HOST = 0, SRW_DEVICE = 1 } srw_where;
@@ -261,6 +262,23 @@ srw_status srw_get_basis(srw_handle h, double* out);
 srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char* cache_path,
                         void* stream, int* chosen);
 
+/* Tensor-core fold configuration `index` (0 .. n-1; SRW_EINVAL past the
+ * last): rec tile width `tile` (128 or 256 reconstructed bins per work item),
+ * `k_block` (true bins per pipeline stage) and `stages` (shared-memory
+ * pipeline depth, for the split precisions).  These are srw_autotune's
+ * candidates.  Every candidate accumulates each output element from the same
+ * updates in the same order, so the folded spectra are bitwise equal across
+ * candidates (-2 ln L differs at most by the order of the per-tile partial
+ * sums); candidates differ in speed only.  Any pointer may be NULL. */
+srw_status srw_fold_config(int index, int* tile, int* k_block, int* stages);
+/* Use configuration `index` for `precision` on this handle (a tensor-core
+ * precision; replaces the autotuned choice until the next srw_autotune). */
+srw_status srw_set_fold_config(srw_handle h, srw_precision precision, int index);
+/* The configuration this handle uses for `precision` (*index) and how many
+ * candidates the last srw_autotune for it timed (*timed; 0 if none ran or the
+ * choice came from the cache file).  Either pointer may be NULL. */
+srw_status srw_get_fold_config(srw_handle h, srw_precision precision, int* index, int* timed);
+
 /* Work of the batched tensor-core fold at `precision` with rec tiles of
  * `tile` bins (128 or 256; 0 = the handle's current configuration):
  * *executed_fraction receives the fraction of the (rec tile, block of 64 true
@@ -293,11 +311,13 @@ srw_status srw_info(srw_handle h, srw_info_t* info);
  * Synchronous; invalidates captured graphs. */
 srw_status srw_set_reference(srw_handle h, const float* theta_ref);
 
-/* Kernel timing.  With profiling enabled, srw_loglik records CUDA events
- * immediately before and after its fold launch (the GEMV of the single-point
- * path, the batched fold otherwise); srw_profile_read waits for the last such
- * launch and returns its device time in milliseconds.  Enabling or disabling
- * profiling selects a different captured graph. */
+/* Kernel timing.  With profiling enabled, srw_loglik launches its kernels
+ * directly (no CUDA graph) and records CUDA events on the call's stream
+ * immediately before and after the fold kernel alone (the GEMV of the
+ * single-point path, the batched fold otherwise; not the scale pre-pass, the
+ * weights kernel or the final reduction); srw_profile_read waits for the last
+ * such launch and returns that kernel's device time in milliseconds.  With
+ * profiling disabled the calls replay their captured graphs. */
 srw_status srw_profile(srw_handle h, int enable);
 srw_status srw_profile_read(srw_handle h, float* fold_ms);
 
@@ -358,12 +378,16 @@ srw_status srw_group_loglik(srw_group g, const float* theta, double* out, int wh
 /* Time the candidate schedules for `precision` and keep the fastest:
  *   0: every configuration with bn = 256;
  *   1: bn per configuration from a cost model of its padded tiles;
- *   2: every configuration with bn = 128 (shallower stages, more of them).
+ *   2: every configuration with bn = 128 (shallower stages, more of them);
+ *   3: bn per configuration by measurement: starting from the fastest of 0-2,
+ *      the tile width of one configuration at a time (the 16 most expensive)
+ *      is flipped and kept where the launch gets more than 1 % shorter.
  * `chosen` (may be NULL) receives the candidate index.  No-op for SRW_FP32. */
 srw_status srw_group_autotune(srw_group g, srw_precision precision, void* stream, int* chosen);
 
-/* Use candidate schedule `candidate` (0, 1 or 2 as above) for `precision`
- * without timing (a fixed choice, or one read back from srw_group_schedule). */
+/* Use candidate schedule `candidate` (0 .. 3 as above; 3 before an autotune
+ * falls back to 1) for `precision` without timing (a fixed choice, or one read
+ * back from srw_group_schedule). */
 srw_status srw_group_set_schedule(srw_group g, srw_precision precision, int candidate);
 
 /* The schedule in use for `precision` (built if needed): widest tile, the tile
@@ -427,6 +451,31 @@ typedef struct {
 srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* opts,
                              float* epoch_loss);
 
+/* Checkpoint / resume of training (the paper has no counterpart: its fits are
+ * stateless; the surrogate's training is not).  srw_surrogate_save writes the
+ * whole training state: FP32 master weights and biases, Adam's first and
+ * second moments and step count, the per-bin standardization and the number
+ * of completed epochs of the last fit.  The file is written as path + ".tmp"
+ * and renamed over `path`, so an interrupted save leaves the previous
+ * checkpoint intact; it carries a checksum.  srw_surrogate_load restores it
+ * into a surrogate of the same network and parameter box (SRW_EINVAL
+ * otherwise, or if the file is damaged); *epochs_done (may be NULL) receives
+ * the completed epochs.
+ * srw_surrogate_fit_resume runs epochs first_epoch .. stop_epoch - 1
+ * (stop_epoch <= 0: to opts->epochs) of the fit that srw_surrogate_fit(opts)
+ * would run on the same points: the same
+ * targets and batches (fixed order, no random state), the learning-rate
+ * schedule continued from step first_epoch x steps, Adam continued from the
+ * loaded state; if checkpoint_path is not NULL a checkpoint is saved after
+ * every epoch.  A fit interrupted after epoch k and resumed from its
+ * checkpoint with first_epoch = k ends with the same weights as the
+ * uninterrupted fit.  epoch_loss (may be NULL) has opts->epochs entries; the
+ * resumed ones are written. */
+srw_status srw_surrogate_save(srw_surrogate s, const char* path);
+srw_status srw_surrogate_load(srw_surrogate s, const char* path, long long* epochs_done);
+srw_status srw_surrogate_fit_resume(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* opts,
+                                    int first_epoch, int stop_epoch, const char* checkpoint_path, float* epoch_loss);
+
 /* Surrogate -2 ln L (eq. logL with mu_j = exp(m_j + s_j y_j), the handle's data
  * and mask) for P points; `where` and `stream` as in srw_loglik. */
 srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, double* out, int where, void* stream);
@@ -476,6 +525,25 @@ typedef struct {
 } srw_scan_result;
 srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* opts, srw_scan_result* res);
 
+/* A resumable scan (the paper has no counterpart).  The points of `opts` are
+ * cut into chunks of chunk_points consecutive Sobol indices; each chunk is
+ * one srw_surrogate_scan with the same options (its own lowest keep_frac and
+ * the same cell rule), and after each chunk its result is recorded in the
+ * text file state_path (rewritten through a temporary file and a rename).  A
+ * call first reads that file, skips the chunks it records, and runs at most
+ * max_new_chunks further chunks (<= 0: all the rest); *complete (may be
+ * NULL) is 1 once every chunk is done.  *res is the result over the completed
+ * chunks: the smallest exact minimum (ties: smaller Sobol index), counts and
+ * times summed.  The file records the scan's options (and a checksum of the
+ * check points): a file of another scan gives SRW_EINVAL.  Each chunk keeps its
+ * own lowest keep_frac, so the number of re-evaluated points can exceed the
+ * single call's; the minimum is the same whenever the rule's error bars hold
+ * (the true minimum's chunk re-evaluates it).  Device memory is bounded by
+ * the chunk, not by n_points. */
+srw_status srw_surrogate_scan_chunked(srw_surrogate s, const srw_scan_opts* opts, long long chunk_points,
+                                      const char* state_path, int max_new_chunks, srw_scan_result* res,
+                                      int* complete);
+
 /* The same scan without the surrogate: the exact path on every point; the
  * minimum, its index and the device time. */
 srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long n_points, int precision,
@@ -497,6 +565,44 @@ srw_status srw_surrogate_destroy(srw_surrogate s);
  * records a timeout and returns; the call then reports SRW_ETIMEOUT (SRW_OK
  * would mean the wait did not expire).  The context remains usable. */
 srw_status srw_diag_wait_timeout(unsigned limit_us);
+
+/* Host-side fault injection (the paper has no counterpart): makes the
+ * library's own failure paths run on demand, for tests, without faulting,
+ * trapping or hanging the GPU.  An armed fault fires once, at the (skip+1)-th
+ * matching event after it was armed, and then disarms:
+ *   SRW_FAULT_ALLOC   a device allocation of the library is not made and
+ *                     reports out-of-memory (the call returns SRW_ENOMEM);
+ *   SRW_FAULT_LAUNCH  a kernel-launch check reports a launch failure (the
+ *                     call returns SRW_ECUDA; a CUDA graph being captured for
+ *                     the call is discarded, never cached);
+ *   SRW_FAULT_TIMEOUT a fold launch (single-point GEMV or tensor-core fold)
+ *                     makes one wait wait on an mbarrier that nothing arrives
+ *                     on, with a 1 ms limit; the wait gives up and the kernel
+ *                     takes its abort path: the affected points' values are
+ *                     NaN, host-pointer calls return SRW_ETIMEOUT, and a
+ *                     graph captured with the fault is run once, not cached.
+ * SRW_FAULT_NONE disarms.  The environment variable SRW_FAULT ("alloc",
+ * "launch" or "timeout", optionally ":N" for skip = N) arms a fault once per
+ * process, before the first library call that allocates or launches; an
+ * explicit srw_fault_inject() overrides it.  After every injected failure the
+ * handle stays usable: the next call computes normally.  Process-wide state
+ * (all handles and threads). */
+typedef enum { SRW_FAULT_NONE = 0, SRW_FAULT_ALLOC = 1, SRW_FAULT_LAUNCH = 2, SRW_FAULT_TIMEOUT = 3 } srw_fault_kind;
+srw_status srw_fault_inject(int kind, long long skip);
+/* *kind = the armed fault kind (SRW_FAULT_NONE once it has fired or if none
+ * is armed). */
+srw_status srw_fault_pending(int* kind);
+/* Parse an SRW_FAULT specification ("kind" or "kind:N") without arming it:
+ * SRW_EINVAL if it is not one; kind and skip may be NULL. */
+srw_status srw_fault_parse(const char* spec, int* kind, long long* skip);
+
+/* Device-side status of the handle's calls with `where` = SRW_DEVICE since the
+ * last srw_check (or the last host-pointer call, which reports and clears its
+ * own): synchronises `stream` (NULL: the handle's stream), reads and clears
+ * the handle's device status word and returns SRW_ETIMEOUT if a bounded
+ * device wait expired (the affected points' values are NaN), else
+ * SRW_EDOMAIN if some value is +inf, else SRW_OK. */
+srw_status srw_check(srw_handle h, void* stream);
 
 const char* srw_last_error(srw_handle h);
 const char* srw_status_string(srw_status s);

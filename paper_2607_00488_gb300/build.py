@@ -18,6 +18,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsrw.so")
+# the debug build: every SRW_CHECK bounds check compiled in (-DSRW_DEBUG_CHECKS)
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libsrw_debug.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,20 +39,23 @@ def _newest_header():
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def build(verbose=False, force=False):
+def build(verbose=False, force=False, debug=False):
+    """Compile libsrw.so (or, with debug=True, libsrw_debug.so with the bounds
+    checks compiled in); returns the library path."""
     nvcc = nvcc_path()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib, extra = (BUILD_DEBUG, LIB_DEBUG, ["-DSRW_DEBUG_CHECKS"]) if debug else (BUILD, LIB, [])
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_t = _newest_header()
     jobs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_t):
             jobs.append((src, obj))
 
     def compile_one(job):
         src, obj = job
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, r.returncode, r.stdout + r.stderr
 
@@ -60,15 +66,22 @@ def build(verbose=False, force=False):
                     sys.stderr.write(out)
                 if rc != 0:
                     raise RuntimeError("nvcc failed on %s" % src)
-    objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in srcs]
-    if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-cudart", "static"]
+    objs = [os.path.join(bdir, os.path.basename(s) + ".o") for s in srcs]
+    if jobs or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib] + objs + ["-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-    return LIB
+    return lib
+
+
+def build_all(verbose=False, force=False):
+    """Both libraries, the release and the debug build, compiled concurrently."""
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        libs = list(ex.map(lambda d: build(verbose, force, d), (False, True)))
+    return libs
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, debug="--debug" in sys.argv))

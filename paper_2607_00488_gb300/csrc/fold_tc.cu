@@ -52,6 +52,9 @@
 
 #include <cuda.h>
 
+#include <cmath>
+#include <vector>
+
 #include "dfloat.cuh"
 #include "poisson.cuh"
 #include "ptx.cuh"
@@ -64,18 +67,34 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128;   // points per tile (MMA M, TMEM lanes)
-constexpr int kBK = 64;    // K per stage: one 128-byte swizzle atom of BF16
+constexpr int kBK = 64;    // true bins per block of the zero-block ranges (and the widest stage)
 constexpr int kWWarps = 8;
 constexpr int kEpiWarp0 = 8;
 constexpr int kTmaWarp = 12;
 constexpr int kMmaWarp = 13;
 constexpr int kThreads = 14 * 32;
-constexpr int kShatBytes = kBK * kNB * 4;  // coefficient spectra of one K block (k-major)
-constexpr int kShatSlots = 4;              // depth of the coefficient-spectra ring
+
+// Pipeline stage of BK true bins (BK = 64: rows of 128 bytes, 128-byte
+// swizzle; BK = 32: rows of 64 bytes, 64-byte swizzle, twice the stages in
+// the same shared memory, so the R tiles' TMA loads are issued further ahead
+// of the MMAs that consume them).  The W producers write 16-byte chunks of 8
+// true bins: BK / 8 chunks per row.  With BK = 64 the eight producer warps
+// take one chunk each; with BK = 32 they form two groups of four that take
+// turns over the stages, so each warp still computes four rows of eight bins
+// (the coefficient-spectra loads of a chunk feed four rows).
+template <int BK>
+struct KStage {
+  static constexpr int kShatBytes = BK * kNB * 4;       // coefficient spectra of one stage (k-major)
+  static constexpr int kShatSlots = 4 * kBK / BK;       // depth of the coefficient-spectra ring (256 true bins)
+  static constexpr int kChunks = BK / 8;                // 16-byte chunks of a tile row
+  static constexpr int kGroups = kWWarps / kChunks;     // producer warp groups taking turns over the stages
+  static constexpr int kPerBlock = kBK / BK;            // stages per block of the zero-block ranges
+};
 
 struct TcMaps {
-  CUtensorMap hi[2], lo[2];      // BF16 split; index 0: box rows 128, 1: box rows 256
-  CUtensorMap hi16[2], lo16[2];  // FP16 split of the row-scaled R
+  // [stage width: 0 = 64, 1 = 32 true bins][box rows: 0 = 128, 1 = 256]
+  CUtensorMap hi[2][2], lo[2][2];      // BF16 split
+  CUtensorMap hi16[2][2], lo16[2][2];  // FP16 split of the row-scaled R
 };
 
 __device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
@@ -127,17 +146,45 @@ __device__ __forceinline__ void coefficients(const float* th, dfloat s, const Co
   }
 }
 
-template <int BN, bool X3>
+template <int BN, bool X3, int BK = kBK>
 struct TcShape {
-  static constexpr int kAB = kBM * kBK * 2;             // bytes of one BF16 A tile
-  static constexpr int kBB = BN * kBK * 2;              // bytes of one BF16 B tile
+  using K = KStage<BK>;
+  static constexpr int kAB = kBM * BK * 2;              // bytes of one BF16 A tile
+  static constexpr int kBB = BN * BK * 2;               // bytes of one BF16 B tile
   static constexpr int kStageBytes = (X3 ? 2 : 1) * (kAB + kBB);
-  static constexpr int kStages = (200 * 1024 - kShatSlots * kShatBytes) / kStageBytes;
-  static constexpr int kSmem = kStages * kStageBytes + kShatSlots * kShatBytes + 1024;  // + alignment slack
-  static constexpr int kTmemCols = 2 * BN;
+  static constexpr int kShatRing = K::kShatSlots * K::kShatBytes;
+  static constexpr int kStages = (200 * 1024 - kShatRing) / kStageBytes;
+  static constexpr int kSmem = kStages * kStageBytes + kShatRing + 1024;  // + alignment slack
+  static constexpr int kAccCols = BN;  // TMEM columns of one item's accumulator
+  static constexpr int kBufs = 2;      // items in flight in TMEM (the epilogue overlaps the next MMAs)
+  static constexpr int kTmemCols = kBufs * kAccCols;
 };
 
+// K blocks of a rec tile in the order the fold accumulates them: kr = {first
+// block, +count} walks up from `first`, {first, -count} walks down (and the
+// 16-wide MMA steps inside a stage then run down too, so that the true bins
+// are accumulated in strictly decreasing order whatever the stage width).
+// kr counts blocks of kBK = 64 true bins; with BK = 32 each is two stages.
+// The direction is chosen per tile at create time (see tc_block_ranges).
+template <int BK>
+__device__ __forceinline__ int kb_count(int2 kr) {
+  return KStage<BK>::kPerBlock * (kr.y >= 0 ? kr.y : -kr.y);
+}
+template <int BK>
+__device__ __forceinline__ int kb_at(int2 kr, int kk) {
+  constexpr int R = KStage<BK>::kPerBlock;
+  return kr.y >= 0 ? R * kr.x + kk : R * kr.x + (R - 1) - kk;
+}
+
 constexpr int kMaxGroups = 4096;  // configurations of one grouped launch
+constexpr int kKbrStaged = 64;    // rec tiles whose K-block walks a single-configuration CTA keeps in shared memory
+
+// K-block walk of the rec tile at n0 (shared-memory copy when staged).
+template <bool GROUPED, int BN>
+__device__ __forceinline__ int2 tile_walk(const TcGroup& G, int n0, const int2* kbr_s) {
+  const int nt = n0 / (GROUPED ? G.bn : BN);
+  return (!GROUPED && nt < kKbrStaged) ? kbr_s[nt] : G.kbr[nt];
+}
 
 // Kernel parameters.  A single-configuration launch walks the m x n tiles of
 // g0 with a grid stride; a grouped launch walks per-CTA item lists.
@@ -151,6 +198,7 @@ struct TcLaunch {
   double* parts;
   float* musig_out;            // single configuration only: [P][n_rec] folded deviations
   unsigned* status;
+  int inject;                  // injected timeout (host-side fault injection): CTA 0's epilogue gives up
 };
 
 // Item loops: a grid stride written directly in blockIdx / gridDim / a kernel
@@ -194,18 +242,30 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
 // TMEM accumulators.  In a grouped launch each configuration's tile width
 // bn <= BN is a runtime value (TMA box, MMA N, epilogue columns); a single
 // configuration uses bn = BN.
-template <int BN, bool X3, bool GROUPED, bool F16>
+template <int BN, int BK, bool X3, bool GROUPED, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
 fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcLaunch L) {
-  using S = TcShape<BN, X3>;
+  using S = TcShape<BN, X3, BK>;
+  using KS = KStage<BK>;
   constexpr int ST = S::kStages;
+  constexpr int NB = S::kBufs;
+  constexpr int kShatSlots = KS::kShatSlots;
+  constexpr int kShatBytes = KS::kShatBytes;
   extern __shared__ unsigned char dsmem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsmem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t r_full[ST], w_full[ST], empty[ST], acc_full[2], acc_empty[2], drain;
-  __shared__ __align__(8) uint64_t s_full[kShatSlots], s_empty[kShatSlots];
+  __shared__ __align__(8) uint64_t r_full[ST], w_full[ST], empty[ST], acc_full[NB], acc_empty[NB], drain;
+  __shared__ __align__(8) uint64_t s_full[kShatSlots], s_empty[kShatSlots], never;
+  // per-bin constants of the epilogue for the current and the next item,
+  // copied ahead by the TMA warp: {n_j, b_j + R W_ref - n_j, mask, 1/r_j}
+  __shared__ __align__(16) float4 nb_s[2][BN];
+  __shared__ __align__(8) uint64_t nb_full[2], nb_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ unsigned abort_flag;
   __shared__ uint32_t map_fenced[GROUPED ? kMaxGroups / 32 : 1];  // maps already acquired by the R producer
+  // K-block walks of a single configuration's rec tiles, staged once per CTA
+  // (every role reads one at each item start; from global memory that is a
+  // load latency on the pipeline's path per item)
+  __shared__ int2 kbr_s[GROUPED ? 1 : kKbrStaged];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned* status = L.status;
@@ -222,21 +282,28 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
 
   if (GROUPED)
     for (int i = threadIdx.x; i < kMaxGroups / 32; i += blockDim.x) map_fenced[i] = 0u;
+  if (!GROUPED)
+    for (int i = threadIdx.x; i < L.g0.n_tiles && i < kKbrStaged; i += blockDim.x) kbr_s[i] = L.g0.kbr[i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       ptx::mbar_init(&r_full[s], 1);
-      ptx::mbar_init(&w_full[s], kWWarps);
+      ptx::mbar_init(&w_full[s], kWWarps / KS::kGroups);
       ptx::mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       ptx::mbar_init(&acc_full[b], 1);
       ptx::mbar_init(&acc_empty[b], 4);
     }
     for (int q = 0; q < kShatSlots; ++q) {
       ptx::mbar_init(&s_full[q], 1);
-      ptx::mbar_init(&s_empty[q], kWWarps);
+      ptx::mbar_init(&s_empty[q], kWWarps / KS::kGroups);
     }
     ptx::mbar_init(&drain, 1);
+    ptx::mbar_init(&never, 1);  // nothing arrives on it (injected timeout)
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&nb_full[b], 1);
+      ptx::mbar_init(&nb_empty[b], 4);
+    }
     abort_flag = 0u;
     ptx::fence_barrier_init();
   }
@@ -254,10 +321,12 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   if (warp < kWWarps) {
     // ------------------------------------------------------------ W producers
     // thread: rows rg, rg + 32, rg + 64, rg + 96 of the A tile and the 8 K of
-    // chunk `warp`; the coefficient-spectra loads are warp-uniform and each
+    // chunk `ch`; the coefficient-spectra loads are warp-uniform and each
     // feeds 32 FMAs (shared-memory wavefronts are the scarce resource here).
+    // With BK = 32 warp group `wg` produces the stages g with g % 2 == wg.
     const int rg = lane;
-    const int ch = warp;  // 16-byte chunk = 8 consecutive k
+    const int ch = warp % KS::kChunks;  // 16-byte chunk = 8 consecutive k
+    const int wg = warp / KS::kChunks;
     int g = 0;            // global K-block counter (stage ring position)
     FOR_ITEMS(idx) {
       if (__any_sync(0xffffffffu, aborted(&abort_flag))) break;
@@ -267,7 +336,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const float* theta = L.theta + (size_t)G.p_off * 5;
       const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
       // K blocks of this rec tile that hold nonzero response (the rest add exact zeros)
-      const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
+      const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
       float c[4][kNB];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
@@ -285,7 +354,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         }
       }
       bool ok = true;
-      for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
+      for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
+        if (KS::kGroups > 1 && g % KS::kGroups != wg) continue;  // the other group's stage
         const int st = g % ST, sl = g % kShatSlots;
         // the A buffers of this stage are free once the MMAs of its previous
         // use have completed; the coefficient spectra come through their own ring
@@ -319,12 +389,12 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             else h[rr][q] = pack_bf16x2(w[rr][0], w[rr][1]);
           }
         }
-        // the four rows share the swizzle phase (row & 7)
-        const uint32_t off = (uint32_t)((ch ^ (rg & 7)) * 16);
+        // the four rows share the swizzle phase (rows 32 apart)
+        const uint32_t off = swz_offset<BK>(rg, ch);
         const uint32_t ah = ptx::smem_addr(a_hi(st)), al = ptx::smem_addr(a_lo(st));
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
-          const uint32_t ro = (uint32_t)((rg + 32 * rr) * 128) + off;
+          const uint32_t ro = (uint32_t)(32 * rr * 2 * BK) + off;
           st_shared_v4(ah + ro, h[rr][0], h[rr][1], h[rr][2], h[rr][3]);
           if (X3) st_shared_v4(al + ro, l[rr][0], l[rr][1], l[rr][2], l[rr][3]);
         }
@@ -340,23 +410,41 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   } else if (warp < kEpiWarp0 + 4) {
     // ------------------------------------------------------------ epilogue
     const int q = warp - kEpiWarp0;  // TMEM lane quarter of this warp
+    // injected timeout (host-side fault injection): one warp of CTA 0 waits for
+    // an arrival that never comes, with a 1 ms limit, and gives up
+    if (L.inject && blockIdx.x == 0 && q == 0 &&
+        !__all_sync(0xffffffffu, ptx::mbar_wait(&never, 0, &abort_flag, 1000000ull)))
+      give_up();
+    // once this CTA has given up, every item it has not finished gets a NaN
+    // partial, so the affected points read NaN instead of a stale value
+    bool dead = false;
     int tc = -1;
     FOR_ITEMS(idx) {
       ++tc;
-      if (__any_sync(0xffffffffu, aborted(&abort_flag))) break;
       int m0, n0, gi;
       const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
       if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
       const int bn = GROUPED ? G.bn : BN, nt = n0 / bn, n_rec = G.n_rec, P = G.P;
-      const float4* nb4 = G.nb4;
-      const int buf = tc & 1;
-      if (!warp_wait(&acc_full[buf], (tc >> 1) & 1, &abort_flag, 256)) {
+      const int buf = tc % NB;
+      const int p = m0 + q * 32 + lane;
+      const int tb = tc & 1;  // constants buffer of this item
+      if (!dead && __any_sync(0xffffffffu, aborted(&abort_flag))) dead = true;
+      if (!dead && !warp_wait(&acc_full[buf], (tc / NB) & 1, &abort_flag, 256)) {
         give_up();
-        break;
+        dead = true;
+      }
+      if (!dead && parts != nullptr && !warp_wait(&nb_full[tb], (tc >> 1) & 1, &abort_flag)) {
+        give_up();
+        dead = true;
+      }
+      SRW_CHECK(status, nt >= 0 && nt < G.n_tiles && m0 >= 0 && m0 < P);
+      if (dead) {
+        if (parts != nullptr && p < P)
+          parts[G.parts_off + (long long)nt * P + p] = __longlong_as_double(0x7ff8000000000000LL);
+        continue;
       }
       tc_fence_after();
-      const int p = m0 + q * 32 + lane;
-      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S::kAccCols);
       float sinv = 1.f;  // 1 / s_p (exact: s_p is a power of two)
       if (F16 && p < P) sinv = 1.f / L.wscale[(size_t)G.p_off + p];
       dfloat acc = {0.f, 0.f};
@@ -370,8 +458,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int j = n0 + c0 + k;
-            // {n_j (0 where masked), b_j + R W_ref, mask, 1/r_j}; padding columns add nothing
-            dj[k] = j < n_rec ? __ldg(nb4 + j) : make_float4(0.f, 1.f, 0.f, 0.f);
+            // {n_j (0 where masked), b_j + R W_ref - n_j, mask, 1/r_j}; padding columns add nothing
+            dj[k] = j < n_rec ? nb_s[tb][c0 + k] : make_float4(0.f, 1.f, 0.f, 0.f);
           }
         } else {  // folded spectra only (no data needed): just the row scales
 #pragma unroll
@@ -392,10 +480,10 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           float ts = 0.f;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            // the power-of-two scales of both operands come out exactly
-            const float mu = F16 ? fmaf(v[k], sinv * dj[k].w, dj[k].y) : v[k] + dj[k].y;
-            ts = fmaf(poisson_term_f32_tc(mu, dj[k].x), dj[k].z, ts);
-            mneg = fminf(mneg, mu * dj[k].z);
+            // mu - n (the power-of-two scales of both operands come out exactly)
+            const float dm = F16 ? fmaf(v[k], sinv * dj[k].w, dj[k].y) : v[k] + dj[k].y;
+            ts = fmaf(poisson_term_f32_dm(dm, dj[k].x), dj[k].z, ts);
+            mneg = fminf(mneg, (dj[k].x + dm) * dj[k].z);
           }
           if (isinf(ts) || isnan(ts)) infinite = true;
           else acc = df_add(acc, ts);
@@ -404,7 +492,10 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       if (mneg < 0.f) infinite = true;
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+      if (lane == 0) {
+        ptx::mbar_arrive(&acc_empty[buf]);
+        if (parts != nullptr) ptx::mbar_arrive(&nb_empty[tb]);
+      }
       if (parts != nullptr && p < P)
         parts[G.parts_off + (long long)nt * P + p] =
             infinite ? __longlong_as_double(0x7ff0000000000000LL) : (double)acc.hi + (double)acc.lo;
@@ -419,8 +510,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
-        const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * kBK * 2);
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+        const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * BK * 2);
         const CUtensorMap* mh = &map_hi;
         const CUtensorMap* ml = &map_lo;
         if (GROUPED) {
@@ -432,16 +523,18 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             map_fenced[gi >> 5] |= 1u << (gi & 31);
           }
         }
-        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
+        for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
+          const int kb = kb_at<BK>(kr, kk);
           const int st = g % ST;
           if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
             give_up();
             ok = false;
             break;
           }
+          SRW_CHECK(status, kb >= 0 && kb < G.k_pad / BK && n0 >= 0 && n0 < G.n_tiles * (GROUPED ? G.bn : BN));
           ptx::mbar_arrive_expect_tx(&r_full[st], bytes);
-          tma_load_2d(b_hi(st), mh, kb * kBK, n0, &r_full[st]);
-          if (X3) tma_load_2d(b_lo(st), ml, kb * kBK, n0, &r_full[st]);
+          tma_load_2d(b_hi(st), mh, kb * BK, n0, &r_full[st]);
+          if (X3) tma_load_2d(b_lo(st), ml, kb * BK, n0, &r_full[st]);
           issued_g = g + 1;
         }
       }
@@ -456,21 +549,43 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
-        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+        for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
+          const int kb = kb_at<BK>(kr, kk);
           const int sl = g % kShatSlots;
           if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
             give_up();
             ok = false;
             break;
           }
+          SRW_CHECK(status, kb >= 0 && (kb + 1) * BK <= G.k_pad);
           ptx::mbar_arrive_expect_tx(&s_full[sl], (uint32_t)kShatBytes);
-          ptx::bulk_g2s(shat_s(sl), G.shat_k8 + (size_t)kb * kBK * 2, (uint32_t)kShatBytes, &s_full[sl]);
+          ptx::bulk_g2s(shat_s(sl), G.shat_k8 + (size_t)kb * BK * 2, (uint32_t)kShatBytes, &s_full[sl]);
           issued = g + 1;
         }
       }
       for (int u = max(0, issued - kShatSlots); u < issued; ++u)
         ptx::mbar_wait(&s_full[u % kShatSlots], (u / kShatSlots) & 1, nullptr, 100000000ull);
+    } else if (lane == 2 && parts != nullptr) {  // the epilogue's per-bin constants, one item ahead
+      int tc = -1, issued = 0;
+      FOR_ITEMS(idx) {
+        ++tc;
+        int m0, n0, gi;
+        const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
+        if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
+        const int tb = tc & 1;
+        if (!ptx::mbar_wait(&nb_empty[tb], ((tc >> 1) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
+          give_up();
+          break;
+        }
+        const int cnt = min(GROUPED ? G.bn : BN, G.n_rec - n0);  // >= 1: tiles start below n_rec
+        SRW_CHECK(status, cnt >= 1 && n0 >= 0);
+        ptx::mbar_arrive_expect_tx(&nb_full[tb], (uint32_t)cnt * 16u);
+        ptx::bulk_g2s(&nb_s[tb][0], G.nb4 + n0, (uint32_t)cnt * 16u, &nb_full[tb]);
+        issued = tc + 1;
+      }
+      for (int u = max(0, issued - 2); u < issued; ++u)  // never end with copies in flight
+        ptx::mbar_wait(&nb_full[u & 1], (u >> 1) & 1, nullptr, 100000000ull);
     }
   } else {
     // ------------------------------------------------------------ MMA issuer
@@ -484,17 +599,18 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = G.kbr[n0 / (GROUPED ? G.bn : BN)];
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
         const uint32_t idesc = idesc_f16kind(kBM, GROUPED ? G.bn : BN, F16);
-        const int buf = tc & 1;
-        if (!ptx::mbar_wait(&acc_empty[buf], ((tc >> 1) & 1) ^ 1, &abort_flag)) {
+        const int buf = tc % NB;
+        if (!ptx::mbar_wait(&acc_empty[buf], ((tc / NB) & 1) ^ 1, &abort_flag)) {
           give_up();
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * S::kAccCols);
+        const bool down = kr.y < 0;  // descending walk: the MMA steps inside a block run down too
         bool ok = true;
-        for (int kb = kr.x; kb < kr.y; ++kb, ++g) {
+        for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
           const int st = g % ST;
           if (!ptx::mbar_wait(&r_full[st], (g / ST) & 1, &abort_flag) ||
               !ptx::mbar_wait(&w_full[st], (g / ST) & 1, &abort_flag)) {
@@ -506,12 +622,14 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           const uint32_t ah = ptx::smem_addr(a_hi(st)), bh = ptx::smem_addr(b_hi(st));
           const uint32_t al = ptx::smem_addr(a_lo(st)), bl = ptx::smem_addr(b_lo(st));
 #pragma unroll
-          for (int ks = 0; ks < kBK / 16; ++ks) {
+          for (int q = 0; q < BK / 16; ++q) {
+            const int ks = down ? BK / 16 - 1 - q : q;
             const uint32_t off = (uint32_t)ks * 32u;  // 16 BF16 along K inside the swizzle atom
-            mma_bf16(d_tmem, smem_desc_sw128(ah + off), smem_desc_sw128(bh + off), idesc, (kb != kr.x) || ks != 0);
+            const uint32_t acc = (kk != 0) || q != 0;  // the item's first update initialises
+            mma_bf16(d_tmem, smem_desc_k<BK>(ah + off), smem_desc_k<BK>(bh + off), idesc, acc);
             if (X3) {
-              mma_bf16(d_tmem, smem_desc_sw128(ah + off), smem_desc_sw128(bl + off), idesc, 1u);
-              mma_bf16(d_tmem, smem_desc_sw128(al + off), smem_desc_sw128(bh + off), idesc, 1u);
+              mma_bf16(d_tmem, smem_desc_k<BK>(ah + off), smem_desc_k<BK>(bl + off), idesc, 1u);
+              mma_bf16(d_tmem, smem_desc_k<BK>(al + off), smem_desc_k<BK>(bh + off), idesc, 1u);
             }
           }
           issued_any = true;
@@ -631,34 +749,58 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int BN, bool X3, bool F16>
-cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(fold_tc_kernel<BN, X3, false, F16>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<BN, X3>::kSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fold_tc_kernel<BN, X3, true, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcShape<BN, X3>::kSmem);
+template <int BN, int BK, bool X3, bool F16, bool GROUPED>
+cudaError_t set_attr1() {
+  return cudaFuncSetAttribute(fold_tc_kernel<BN, BK, X3, GROUPED, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcShape<BN, X3, BK>::kSmem);
 }
 
-template <int BN, bool X3, bool GROUPED, bool F16>
+// Every instantiation a launch can select: both stage widths for single
+// configurations; grouped launches use 64-wide stages.
+template <int BN>
+cudaError_t set_attr_all() {
+  cudaError_t e = cudaSuccess;
+#define SRW_ATTR(...) \
+  if (e == cudaSuccess) e = set_attr1<__VA_ARGS__>()
+  SRW_ATTR(BN, 64, true, false, false);
+  SRW_ATTR(BN, 64, true, true, false);
+  SRW_ATTR(BN, 64, false, false, false);
+  SRW_ATTR(BN, 32, true, false, false);
+  SRW_ATTR(BN, 32, true, true, false);
+  SRW_ATTR(BN, 32, false, false, false);
+  SRW_ATTR(BN, 64, true, false, true);
+  SRW_ATTR(BN, 64, true, true, true);
+  SRW_ATTR(BN, 64, false, false, true);
+#undef SRW_ATTR
+  return e;
+}
+
+template <int BN, int BK, bool X3, bool GROUPED, bool F16>
 cudaError_t launch_kernel(const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid, cudaStream_t s) {
-  fold_tc_kernel<BN, X3, GROUPED, F16><<<grid, kThreads, TcShape<BN, X3>::kSmem, s>>>(mh, ml, L);
-  return cudaGetLastError();
+  fold_tc_kernel<BN, BK, X3, GROUPED, F16><<<grid, kThreads, TcShape<BN, X3, BK>::kSmem, s>>>(mh, ml, L);
+  return launch_result();
 }
 
-template <int BN, bool GROUPED>
+template <int BN, int BK, bool GROUPED>
 cudaError_t launch_prec(int precision, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L, int grid,
                         cudaStream_t s) {
-  if (precision == SRW_FP16X3) return launch_kernel<BN, true, GROUPED, true>(mh, ml, L, grid, s);
-  if (precision == SRW_BF16X3) return launch_kernel<BN, true, GROUPED, false>(mh, ml, L, grid, s);
-  return launch_kernel<BN, false, GROUPED, false>(mh, ml, L, grid, s);
+  if (precision == SRW_FP16X3) return launch_kernel<BN, BK, true, GROUPED, true>(mh, ml, L, grid, s);
+  if (precision == SRW_BF16X3) return launch_kernel<BN, BK, true, GROUPED, false>(mh, ml, L, grid, s);
+  return launch_kernel<BN, BK, false, GROUPED, false>(mh, ml, L, grid, s);
 }
 
-template <bool GROUPED>
-cudaError_t launch_any(int bn_max, int precision, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L,
-                       int grid, cudaStream_t s) {
-  if (bn_max == 256) return launch_prec<256, GROUPED>(precision, mh, ml, L, grid, s);
-  return launch_prec<128, GROUPED>(precision, mh, ml, L, grid, s);
+cudaError_t launch_single(int bn, int bk, int precision, const CUtensorMap& mh, const CUtensorMap& ml,
+                          const TcLaunch& L, int grid, cudaStream_t s) {
+  if (bn == 256) return bk == 32 ? launch_prec<256, 32, false>(precision, mh, ml, L, grid, s)
+                                 : launch_prec<256, 64, false>(precision, mh, ml, L, grid, s);
+  return bk == 32 ? launch_prec<128, 32, false>(precision, mh, ml, L, grid, s)
+                  : launch_prec<128, 64, false>(precision, mh, ml, L, grid, s);
+}
+
+cudaError_t launch_grouped(int bn_max, int precision, const CUtensorMap& mh, const CUtensorMap& ml, const TcLaunch& L,
+                           int grid, cudaStream_t s) {
+  if (bn_max == 256) return launch_prec<256, 64, true>(precision, mh, ml, L, grid, s);
+  return launch_prec<128, 64, true>(precision, mh, ml, L, grid, s);
 }
 
 EncodeTiledFn encode_fn() {
@@ -676,9 +818,14 @@ EncodeTiledFn encode_fn() {
 
 bool tc_supported(const srw_ctx* h) { return h->cc_major == 10 && h->cc_minor == 3; }
 
+// Tensor-core fold configurations (the autotuner's candidates).  Every
+// candidate accumulates each output element from the same updates in the
+// same order, so they differ in speed only.
 static const FoldConfig kConfigs[] = {
-    {1, 256, 0, kWWarps},
-    {1, 128, 0, kWWarps},
+    {1, 256, 64, TcShape<256, true, 64>::kStages, kWWarps},
+    {1, 256, 32, TcShape<256, true, 32>::kStages, kWWarps},
+    {1, 128, 64, TcShape<128, true, 64>::kStages, kWWarps},
+    {1, 128, 32, TcShape<128, true, 32>::kStages, kWWarps},
 };
 
 int tc_num_configs() { return (int)(sizeof(kConfigs) / sizeof(kConfigs[0])); }
@@ -690,20 +837,22 @@ cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s) {
                                                              h->d_rhi, h->d_rlo);
   split_r16_kernel<<<h->rec_pad, 256, 0, s>>>(h->d_R, h->n_rec, h->ld_r, h->k_pad, h->d_rhi16, h->d_rlo16, h->d_rinv);
   shat_k8_kernel<<<(h->k_pad + 255) / 256, 256, 0, s>>>(h->d_shat, h->k_pad, h->d_shat_k8);
-  return cudaGetLastError();
+  return launch_result();
 }
 
-cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo) {
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo, int bk) {
   EncodeTiledFn encode = encode_fn();
   if (encode == nullptr) return cudaErrorNotSupported;
+  if (bk != 64 && bk != 32) return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)h->k_pad, (cuuint64_t)h->rec_pad};
   const cuuint64_t strides[1] = {(cuuint64_t)h->k_pad * 2};
   const cuuint32_t estr[2] = {1, 1};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)bn};
+  const cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)bn};  // a box row is one swizzle span (128 or 64 bytes)
   for (int l = 0; l < 2; ++l) {
     void* base = f16 ? (l ? (void*)h->d_rlo16 : (void*)h->d_rhi16) : (l ? (void*)h->d_rlo : (void*)h->d_rhi);
     CUresult r = encode(l ? lo : hi, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
-                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
@@ -711,18 +860,16 @@ cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, 
 }
 
 cudaError_t tc_prepare(srw_ctx* h) {
-  cudaError_t ea = set_attr<256, true, false>();
-  if (ea == cudaSuccess) ea = set_attr<256, false, false>();
-  if (ea == cudaSuccess) ea = set_attr<256, true, true>();
-  if (ea == cudaSuccess) ea = set_attr<128, true, false>();
-  if (ea == cudaSuccess) ea = set_attr<128, false, false>();
-  if (ea == cudaSuccess) ea = set_attr<128, true, true>();
+  cudaError_t ea = set_attr_all<256>();
+  if (ea == cudaSuccess) ea = set_attr_all<128>();
   if (ea != cudaSuccess) return ea;
   TcMaps* maps = new (std::nothrow) TcMaps();
   if (!maps) return cudaErrorMemoryAllocation;
+  for (int ki = 0; ki < 2; ++ki)
   for (int bi = 0; bi < 2; ++bi) {
-    cudaError_t e = tc_encode_maps(h, bi ? 256 : 128, false, &maps->hi[bi], &maps->lo[bi]);
-    if (e == cudaSuccess) e = tc_encode_maps(h, bi ? 256 : 128, true, &maps->hi16[bi], &maps->lo16[bi]);
+    const int bk = ki ? 32 : 64;
+    cudaError_t e = tc_encode_maps(h, bi ? 256 : 128, false, &maps->hi[ki][bi], &maps->lo[ki][bi], bk);
+    if (e == cudaSuccess) e = tc_encode_maps(h, bi ? 256 : 128, true, &maps->hi16[ki][bi], &maps->lo16[ki][bi], bk);
     if (e != cudaSuccess) {
       delete maps;
       return e;
@@ -737,30 +884,76 @@ void tc_release(srw_ctx* h) {
   h->tmap = nullptr;
 }
 
+// Accumulation order of one rec tile's K blocks.  The tensor core's FP32
+// accumulation drops the bits of every update below the accumulator's last
+// place, so the error a row collects grows with the number of updates made
+// after its sum has become large.  Walking the blocks from the tiny end of a
+// row's response towards its peak keeps the sum small while most updates are
+// made; which end that is depends on the response (a one-sided tail, several
+// bands).  The choice is made here, at create time, by replaying the tile's
+// accumulation of R (weights 1, steps of 16 true bins, each update rounded
+// toward zero to FP32) in both directions and keeping the one whose summed
+// error over the tile's rows is smaller; ties keep ascending order.
+static bool descending_is_better(const std::vector<float>& R, int ld, int n_rec, int row0, int rows, int kb0,
+                                 int kb1) {
+  auto rz = [](double x) {
+    float f = (float)x;
+    if (std::fabs((double)f) > std::fabs(x)) f = std::nextafter(f, 0.f);
+    return f;
+  };
+  double err[2] = {0.0, 0.0};
+  for (int r = row0; r < row0 + rows && r < n_rec; ++r) {
+    const float* row = R.data() + (size_t)r * ld;
+    for (int dir = 0; dir < 2; ++dir) {
+      float acc = 0.f;
+      double exact = 0.0;
+      const int nsteps = (kb1 - kb0) * (kBK / 16);
+      for (int q = 0; q < nsteps; ++q) {
+        const int step = dir ? (kb1 * (kBK / 16) - 1 - q) : (kb0 * (kBK / 16) + q);
+        double part = 0.0;
+        for (int k = step * 16; k < step * 16 + 16 && k < ld; ++k) part += (double)row[k];
+        if (part == 0.0) continue;
+        exact += part;
+        acc = rz((double)acc + part);
+      }
+      err[dir] += std::fabs(exact - (double)acc);
+    }
+  }
+  return err[1] < err[0];
+}
+
 // K-block range {first, end} of each rec tile of width bn: the blocks of 64
 // true bins in which some row of the tile has a nonzero hi or lo element.
 // Outside the range every product is an exact zero, so the folds skip those
 // blocks without changing a bit of the accumulation.  A tile without any
 // nonzero element keeps one block (its accumulator must still be written).
+// The device copy holds the walk {first block, +-count} (see kb_at).
 cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s) {
   const int n_kb = h->k_pad / kBK;
   unsigned char* d_flags = nullptr;
   const int max_tiles = (h->n_rec + 127) / 128;
-  cudaError_t e = cudaMalloc(&d_flags, (size_t)max_tiles * n_kb);
+  cudaError_t e = dev_malloc(&d_flags, (size_t)max_tiles * n_kb);
   if (e != cudaSuccess) return e;
   std::vector<unsigned char> flags((size_t)max_tiles * n_kb);
+  std::vector<float> R((size_t)h->n_rec * h->ld_r);
+  e = cudaMemcpyAsync(R.data(), h->d_R, sizeof(float) * R.size(), cudaMemcpyDeviceToHost, s);
+  // direction per group of 256 rows (both tile widths use it, so that every
+  // output element accumulates the same updates in the same order whichever
+  // width a launch uses; skipped blocks only ever add exact zeros)
+  std::vector<char> down[2];
   for (int f16 = 0; f16 < 2 && e == cudaSuccess; ++f16)
-    for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
+    for (int bi = 1; bi >= 0 && e == cudaSuccess; --bi) {
       const int bn = bi ? 256 : 128, n_tiles = (h->n_rec + bn - 1) / bn;
       const uint4* hi = reinterpret_cast<const uint4*>(f16 ? (const void*)h->d_rhi16 : (const void*)h->d_rhi);
       const uint4* lo = reinterpret_cast<const uint4*>(f16 ? (const void*)h->d_rlo16 : (const void*)h->d_rlo);
       kb_flags_kernel<<<dim3(n_kb, n_tiles), 256, 0, s>>>(hi, lo, h->n_rec, h->k_pad, bn, d_flags);
-      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = launch_result()) != cudaSuccess) break;
       if ((e = cudaMemcpyAsync(flags.data(), d_flags, (size_t)n_tiles * n_kb, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
           (e = cudaStreamSynchronize(s)) != cudaSuccess)
         break;
       std::vector<int2>& r = h->kbr_h[f16][bi];
       r.assign(n_tiles, make_int2(0, 1));
+      std::vector<int2> walk(n_tiles, make_int2(0, 1));
       for (int t = 0; t < n_tiles; ++t) {
         int first = -1, last = -1;
         for (int kb = 0; kb < n_kb; ++kb)
@@ -768,11 +961,18 @@ cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s) {
             if (first < 0) first = kb;
             last = kb;
           }
-        if (first >= 0) r[t] = make_int2(first, last + 1);
+        if (first >= 0) {
+          r[t] = make_int2(first, last + 1);
+          if (bi) down[f16].push_back(descending_is_better(R, h->ld_r, h->n_rec, t * bn, bn, first, last + 1));
+          walk[t] = down[f16][bi ? t : t / 2] ? make_int2(last, -(last + 1 - first))
+                                              : make_int2(first, last + 1 - first);
+        } else if (bi) {
+          down[f16].push_back(0);
+        }
       }
-      if ((e = cudaMalloc(&h->d_kbr[f16][bi], sizeof(int2) * n_tiles)) != cudaSuccess) break;
+      if ((e = dev_malloc(&h->d_kbr[f16][bi], sizeof(int2) * n_tiles)) != cudaSuccess) break;
       h->device_bytes += sizeof(int2) * n_tiles;
-      e = cudaMemcpy(h->d_kbr[f16][bi], r.data(), sizeof(int2) * n_tiles, cudaMemcpyHostToDevice);
+      e = cudaMemcpy(h->d_kbr[f16][bi], walk.data(), sizeof(int2) * n_tiles, cudaMemcpyHostToDevice);
     }
   cudaFree(d_flags);
   return e;
@@ -811,7 +1011,8 @@ TcGroup tc_group_of(const srw_ctx* h, int bn, bool f16) {
 }
 
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
-                           double* parts, cudaStream_t s, int* n_parts, float* musig_out) {
+                           double* parts, cudaStream_t s, int* n_parts, float* musig_out, cudaEvent_t ev_begin,
+                           cudaEvent_t ev_end) {
   const TcMaps* maps = static_cast<const TcMaps*>(h->tmap);
   if (!maps) return cudaErrorNotSupported;
   const int bn = cfg.bn == 256 ? 256 : 128, bi = bn == 256 ? 1 : 0;
@@ -827,21 +1028,28 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   L.parts = parts;
   L.musig_out = musig_out;
   L.status = h->d_status;
+  L.inject = inject_timeout();
   if (n_parts) *n_parts = L.g0.n_tiles;
   if (f16) {
     if (h->d_wscale == nullptr || h->wscale_cap < P) return cudaErrorInvalidValue;
     wscale_kernel<<<(P + 255) / 256, 256, 0, s>>>(L.g0, theta, h->d_wscale);
   }
   const int grid = L.n_items < h->sm_count ? L.n_items : h->sm_count;
-  return launch_any<false>(bn, precision, f16 ? maps->hi16[bi] : maps->hi[bi], f16 ? maps->lo16[bi] : maps->lo[bi], L,
-                           grid, s);
+  cudaError_t e;
+  // optional events around the fold kernel alone (not the scale pre-pass)
+  if (ev_begin && (e = cudaEventRecord(ev_begin, s)) != cudaSuccess) return e;
+  const int bk = cfg.bk == 32 ? 32 : 64, ki = bk == 32 ? 1 : 0;
+  e = launch_single(bn, bk, precision, f16 ? maps->hi16[ki][bi] : maps->hi[ki][bi],
+                    f16 ? maps->lo16[ki][bi] : maps->lo[ki][bi], L, grid, s);
+  if (e == cudaSuccess && ev_end) e = cudaEventRecord(ev_end, s);
+  return e;
 }
 
 cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
                                 cudaStream_t s) {
   if (n_groups < 1 || max_P < 1) return cudaSuccess;
   group_wscale_kernel<<<dim3((max_P + 255) / 256, n_groups), 256, 0, s>>>(d_groups, theta, out);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_groups, const int4* d_items, int n_slots,
@@ -857,8 +1065,9 @@ cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_gro
   L.parts = parts;
   L.musig_out = nullptr;
   L.status = status;
+  L.inject = inject_timeout();
   static const CUtensorMap unused{};  // grouped launches read each configuration's maps from its descriptor
-  return launch_any<true>(bn_max == 256 ? 256 : 128, precision, unused, unused, L, n_cta, s);
+  return launch_grouped(bn_max == 256 ? 256 : 128, precision, unused, unused, L, n_cta, s);
 }
 
 int tc_max_groups() { return kMaxGroups; }

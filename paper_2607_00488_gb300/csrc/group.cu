@@ -51,7 +51,7 @@ cudaError_t launch_group_reduce(const GroupPart* d_gparts, int n_groups, int max
   if (n_groups < 1 || max_P < 1) return cudaSuccess;
   const int thr = 256;
   group_reduce_kernel<<<dim3((max_P + thr - 1) / thr, n_groups), thr, 0, s>>>(d_gparts, parts, out, status);
-  return cudaGetLastError();
+  return srw::launch_result();
 }
 
 }  // namespace srw
@@ -80,6 +80,7 @@ struct srw_group_ctx {
   std::vector<unsigned long long> versions;
   bool tensor_ok = true;
   srw_group_plan plan[3];           // SRW_BF16, SRW_BF16X3, SRW_FP16X3
+  std::vector<int> tuned_bn[3];     // candidate 3: tile width per configuration chosen by measurement
   GroupPart* d_simt_gparts = nullptr;  // SRW_FP32
   size_t simt_parts = 0;
   double* d_parts = nullptr;
@@ -149,7 +150,7 @@ void refresh_if_changed(srw_group g) {
 srw_status ensure_parts(srw_group g, size_t n) {
   if (n <= g->parts_cap) return SRW_OK;
   gfree(g->d_parts);
-  G_CUDA(g, cudaMalloc(&g->d_parts, sizeof(double) * n), "grouped partial sums");
+  G_CUDA(g, srw::dev_malloc(&g->d_parts, sizeof(double) * n), "grouped partial sums");
   g->parts_cap = n;
   return SRW_OK;
 }
@@ -164,9 +165,15 @@ double tiles_cost(const srw_ctx* h, int bn, bool f16) {
   return c;
 }
 
-void candidate_widths(srw_group g, int cand, bool f16, int* bn_max, std::vector<int>& bn) {
+void candidate_widths(srw_group g, int cand, int pi, bool f16, int* bn_max, std::vector<int>& bn) {
   bn.assign(g->n, 256);
   *bn_max = 256;
+  if (cand == 3 && (int)g->tuned_bn[pi].size() == g->n) {
+    bn = g->tuned_bn[pi];
+    *bn_max = *std::max_element(bn.begin(), bn.end());
+    return;
+  }
+  if (cand == 3) cand = 1;  // not tuned yet: the cost model's widths
   if (cand == 2) {
     bn.assign(g->n, 128);
     *bn_max = 128;
@@ -184,7 +191,7 @@ srw_status build_plan(srw_group g, int pi, int cand) {
   free_plan(pl);
   pl.candidate = cand;
   const bool f16 = pi + 1 == SRW_FP16X3;
-  candidate_widths(g, cand, f16, &pl.bn_max, pl.bn);
+  candidate_widths(g, cand, pi, f16, &pl.bn_max, pl.bn);
 
   struct Item {
     double cost;
@@ -234,14 +241,14 @@ srw_status build_plan(srw_group g, int pi, int cand) {
   for (int b = 0; b < n_cta; ++b)
     for (size_t k = 0; k < per[b].size(); ++k) items[k * n_cta + b] = per[b][k];
 
-  G_CUDA(g, cudaMalloc(&pl.d_maps, sizeof(CUtensorMap) * maps.size()), "alloc maps");
+  G_CUDA(g, srw::dev_malloc(&pl.d_maps, sizeof(CUtensorMap) * maps.size()), "alloc maps");
   for (int i = 0; i < g->n; ++i) {
     desc[i].map_hi = pl.d_maps + 2 * (size_t)i;
     desc[i].map_lo = pl.d_maps + 2 * (size_t)i + 1;
   }
-  G_CUDA(g, cudaMalloc(&pl.d_groups, sizeof(TcGroup) * desc.size()), "alloc descriptors");
-  G_CUDA(g, cudaMalloc(&pl.d_gparts, sizeof(GroupPart) * gparts.size()), "alloc descriptors");
-  G_CUDA(g, cudaMalloc(&pl.d_items, sizeof(int4) * std::max<size_t>(1, items.size())), "alloc items");
+  G_CUDA(g, srw::dev_malloc(&pl.d_groups, sizeof(TcGroup) * desc.size()), "alloc descriptors");
+  G_CUDA(g, srw::dev_malloc(&pl.d_gparts, sizeof(GroupPart) * gparts.size()), "alloc descriptors");
+  G_CUDA(g, srw::dev_malloc(&pl.d_items, sizeof(int4) * std::max<size_t>(1, items.size())), "alloc items");
   G_CUDA(g, cudaMemcpy(pl.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice), "upload");
   G_CUDA(g, cudaMemcpy(pl.d_groups, desc.data(), sizeof(TcGroup) * desc.size(), cudaMemcpyHostToDevice), "upload");
   G_CUDA(g, cudaMemcpy(pl.d_gparts, gparts.data(), sizeof(GroupPart) * gparts.size(), cudaMemcpyHostToDevice),
@@ -264,7 +271,7 @@ srw_status build_simt(srw_group g) {
     gp[i] = GroupPart{off, np, g->P[i], g->p_off[i], 0, g->hs[i]->d_cdata};
     off += (long long)np * g->P[i];
   }
-  G_CUDA(g, cudaMalloc(&g->d_simt_gparts, sizeof(GroupPart) * gp.size()), "alloc descriptors");
+  G_CUDA(g, srw::dev_malloc(&g->d_simt_gparts, sizeof(GroupPart) * gp.size()), "alloc descriptors");
   G_CUDA(g, cudaMemcpy(g->d_simt_gparts, gp.data(), sizeof(GroupPart) * gp.size(), cudaMemcpyHostToDevice), "upload");
   g->simt_parts = (size_t)off;
   return SRW_OK;
@@ -362,11 +369,11 @@ srw_status srw_group_create(const srw_handle* handles, int n, const int* P, srw_
   g->P_max = pmax;
   cudaError_t e = cudaSetDevice(g->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_theta, sizeof(float) * 5 * total);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_wscale, sizeof(float) * total);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_out, sizeof(double) * total);
+  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_theta, sizeof(float) * 5 * total);
+  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_wscale, sizeof(float) * total);
+  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_out, sizeof(double) * total);
   if (e != cudaSuccess) {
     srw_group_destroy(g);
     return e == cudaErrorMemoryAllocation ? SRW_ENOMEM : SRW_ECUDA;
@@ -389,6 +396,8 @@ srw_status srw_group_loglik(srw_group g, const float* theta, double* out, int wh
   if (where == SRW_HOST) {
     for (size_t q = 0; q < (size_t)g->P_total * 5; ++q)
       if (!std::isfinite(theta[q])) return gfail(g, SRW_EINVAL, "theta must be finite");
+    // a host-pointer call reports the device status of this call only
+    G_CUDA(g, cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), s), "status reset");
     G_CUDA(g, cudaMemcpyAsync(g->d_theta, theta, sizeof(float) * 5 * (size_t)g->P_total, cudaMemcpyHostToDevice, s),
            "theta upload");
     th = g->d_theta;
@@ -425,22 +434,58 @@ srw_status srw_group_autotune(srw_group g, srw_precision precision, void* stream
   G_CUDA(g, cudaEventCreate(&e0), "event");
   G_CUDA(g, cudaEventCreate(&e1), "event");
   const int pi = (int)precision - 1;
-  float best = 1e30f;
-  int best_c = 1;
-  for (int c = 0; c < 3; ++c) {
-    if (build_plan(g, pi, c) != SRW_OK) continue;
-    if (run(g, g->d_theta, g->d_out, (int)precision, s) != SRW_OK) continue;  // warm-up
+  // time the plan built for candidate c (+inf if it fails or a wait timed out)
+  auto time_plan = [&](int c) {
+    if (build_plan(g, pi, c) != SRW_OK) return 1e30f;
+    if (run(g, g->d_theta, g->d_out, (int)precision, s) != SRW_OK) return 1e30f;  // warm-up
     cudaEventRecord(e0, s);
     bool ok = true;
     for (int r = 0; r < 3 && ok; ++r) ok = run(g, g->d_theta, g->d_out, (int)precision, s) == SRW_OK;
     cudaEventRecord(e1, s);
     bool dom = false;
-    if (!ok || check_status(g, s, &dom) != SRW_OK) continue;  // a timed-out schedule is never chosen
+    if (!ok || check_status(g, s, &dom) != SRW_OK) return 1e30f;  // a timed-out schedule is never chosen
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  float best = 1e30f;
+  int best_c = 1;
+  for (int c = 0; c < 3; ++c) {
+    const float ms = time_plan(c);
     if (ms < best) {
       best = ms;
       best_c = c;
+    }
+  }
+  // candidate 3: from the best fixed schedule, flip the tile width of one
+  // configuration at a time (the most expensive ones first, at most 16) and
+  // keep each flip that shortens the launch by more than 1 %
+  {
+    int bn_max = 256;
+    std::vector<int> bn;
+    candidate_widths(g, best_c, pi, pi + 1 == SRW_FP16X3, &bn_max, bn);
+    std::vector<std::pair<double, int>> order;
+    for (int i = 0; i < g->n; ++i)
+      if (g->P[i] > 0)
+        order.push_back({tiles_cost(g->hs[i], bn[i], pi + 1 == SRW_FP16X3) * (double)g->P[i], i});
+    std::sort(order.rbegin(), order.rend());
+    if (order.size() > 16) order.resize(16);
+    g->tuned_bn[pi] = bn;
+    float cur = best;
+    for (const auto& o : order) {
+      const int i = o.second;
+      g->tuned_bn[pi][i] = bn[i] == 256 ? 128 : 256;
+      const float ms = time_plan(3);
+      if (ms < 0.99f * cur) {
+        cur = ms;
+        bn[i] = g->tuned_bn[pi][i];
+      } else {
+        g->tuned_bn[pi][i] = bn[i];
+      }
+    }
+    if (cur < best) {
+      best = cur;
+      best_c = 3;
     }
   }
   cudaEventDestroy(e0);
@@ -455,7 +500,7 @@ srw_status srw_group_set_schedule(srw_group g, srw_precision precision, int cand
   if (!g) return SRW_EINVAL;
   if (precision != SRW_BF16 && precision != SRW_BF16X3 && precision != SRW_FP16X3)
     return gfail(g, SRW_EINVAL, "schedules exist for the tensor-core precisions only");
-  if (candidate < 0 || candidate > 2) return gfail(g, SRW_EINVAL, "candidate must be 0, 1 or 2");
+  if (candidate < 0 || candidate > 3) return gfail(g, SRW_EINVAL, "candidate must be 0, 1, 2 or 3");
   refresh_if_changed(g);
   return build_plan(g, (int)precision - 1, candidate);
 }

@@ -79,7 +79,7 @@ __global__ void basis_eval_kernel(const float* __restrict__ theta, double s2, co
 cudaError_t launch_joint_colsums(const double* hist, const double* mask, const double* live, int n_rec, int n_t,
                                  double* colZ, double* colY, cudaStream_t s) {
   joint_colsum_kernel<<<(n_t + 127) / 128, 128, 0, s>>>(hist, mask, live, n_rec, n_t, colZ, colY);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_joint_gather(const double* hist, const double* mask, const double* live, int n_rec, int n_t,
@@ -88,13 +88,13 @@ cudaError_t launch_joint_gather(const double* hist, const double* mask, const do
   if (n_cols <= 0) return cudaSuccess;
   const dim3 grid((unsigned)((n_cols + 127) / 128), (unsigned)(n_rec < 1024 ? n_rec : 1024));
   joint_gather_kernel<<<grid, 128, 0, s>>>(hist, mask, live, n_rec, n_t, cols, n_cols, factor, R, ld, col0);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_basis_eval(const srw_ctx* h, const float* theta, int mode, float* out, cudaStream_t s) {
   basis_eval_kernel<<<(h->n_t + 255) / 256, 256, 0, s>>>(theta, h->sin2w, h->d_basis, h->d_ssm64, h->d_esm64, h->n_t,
                                                          mode, out);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 }  // namespace srw

@@ -47,12 +47,13 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
                   const double* __restrict__ muref, const double* __restrict__ n64, const double* __restrict__ b64,
                   const unsigned char* __restrict__ mask, const double* __restrict__ c_data,
                   float* __restrict__ musig_out, float* __restrict__ mu_out, double* __restrict__ parts,
-                  unsigned* __restrict__ ticket, double* __restrict__ out, unsigned* __restrict__ status) {
+                  unsigned* __restrict__ ticket, double* __restrict__ out, unsigned* __restrict__ status,
+                  int inject) {
   extern __shared__ __align__(128) unsigned char dsmem[];
   const int chunk = ld < kGvChunk ? ld : kGvChunk;
   float* sbuf = reinterpret_cast<float*>(dsmem);
   float2* spart = reinterpret_cast<float2*>(dsmem + sizeof(float) * (size_t)kGvStages * chunk);
-  __shared__ __align__(8) uint64_t full[kGvStages], empty[kGvStages];
+  __shared__ __align__(8) uint64_t full[kGvStages], empty[kGvStages], never;
   __shared__ unsigned abort_flag;
   __shared__ double sred[kGvThreads / 32];
   __shared__ bool is_last;
@@ -69,6 +70,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
       ptx::mbar_init(&full[st], 1);
       ptx::mbar_init(&empty[st], kGvConsumers);
     }
+    ptx::mbar_init(&never, 1);  // nothing arrives on it (injected timeout)
     abort_flag = 0u;
     ptx::fence_barrier_init();
   }
@@ -87,6 +89,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
         }
         const int row = r0 + u / cpr, k0 = (u % cpr) * chunk;
         const int len = min(chunk, ld - k0);
+        SRW_CHECK(status, row < n_rec && k0 >= 0 && len > 0 && k0 + len <= ld && (len & 3) == 0);
         ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)len * 4u);
         ptx::bulk_g2s(sbuf + (size_t)st * chunk, R + (size_t)row * ld + k0, (uint32_t)len * 4u, &full[st]);
         issued = u + 1;
@@ -101,6 +104,13 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
     // (returns at once without such a dependency); the producer's R stream
     // does not depend on it and is already running
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    // injected timeout (host-side fault injection, block 0): consumer warp 0
+    // waits for an arrival that never comes, with a 1 ms limit, and gives up
+    // exactly as when a copy never completes
+    if (inject && blockIdx.x == 0 && warp == 0 && !ptx::mbar_wait(&never, 0, &abort_flag, 1000000ull)) {
+      atomicExch(&abort_flag, 1u);
+      atomicOr(status, kStatusTimeout);
+    }
     dfloat lacc = {0.f, 0.f};
     for (int u = 0; u < n_units; ++u) {
       const int st = u % kGvStages;
@@ -128,6 +138,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
       if (lane == 0) ptx::mbar_arrive(&empty[st]);
       lacc = df_add(lacc, (ax + ay) + (az + aw));
       if (c == cpr - 1) {
+        SRW_CHECK(status, u / cpr < rows_per_block);
         const dfloat v = df_warp_sum(lacc);
         if (lane == 0) spart[(u / cpr) * kGvConsumers + warp] = make_float2(v.hi, v.lo);
         lacc = {0.f, 0.f};
@@ -136,8 +147,9 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   }
   __syncthreads();
 
-  // ---- epilogue: mu_j, FP64 Poisson terms, block partial
-  double t = 0.0;
+  // ---- epilogue: mu_j, FP64 Poisson terms, block partial (NaN for a block
+  // that gave up, so that the point's value is NaN, never a wrong number)
+  double t = abort_flag != 0u ? __longlong_as_double(0x7ff8000000000000LL) : 0.0;
   if (abort_flag == 0u) {
     for (int rl = threadIdx.x; rl < nrows; rl += kGvThreads) {
       const int j = r0 + rl;
@@ -196,6 +208,7 @@ __global__ void reduce_parts_kernel(const double* __restrict__ parts, int n_part
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   double s = 0.0;
+  SRW_CHECK(status, n_parts >= 1);
   for (int t = 0; t < n_parts; ++t) s += parts[(size_t)t * P + p];
   const double v = 2.0 * s + *c_data;
   if (isinf(v)) atomicOr(status, kStatusDomain);
@@ -225,7 +238,9 @@ __global__ void data_ref_kernel(const double* __restrict__ n64, const double* __
   const bool on = mask == nullptr || mask[j] != 0;
   nbm[j] = make_float4((float)n64[j], (float)br, on ? 1.f : 0.f, 0.f);
   nb2[j] = make_float2(on ? (float)n64[j] : -1.f, (float)br);
-  if (nb4) nb4[j] = make_float4(on ? (float)n64[j] : 0.f, (float)br, on ? 1.f : 0.f, rinv ? rinv[j] : 1.f);
+  // tensor-core epilogue: mu - n is formed from b + R W_ref - n, rounded once from FP64
+  if (nb4) nb4[j] = make_float4(on ? (float)n64[j] : 0.f, (float)(on ? br - n64[j] : br), on ? 1.f : 0.f,
+                                rinv ? rinv[j] : 1.f);
 }
 
 // C = 2 sum_j M_j [n_j - n_j ln n_j + lnGamma(n_j + 1)], one block.
@@ -277,8 +292,8 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
   const double* muref = delta ? h->d_muref64 : nullptr;
   fold_point_kernel<<<fold_point_grid(h), kGvThreads, smem, s>>>(
       h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
-      mu_out, h->d_part, h->d_ticket, out, h->d_status);
-  return cudaGetLastError();
+      mu_out, h->d_part, h->d_ticket, out, h->d_status, inject_timeout());
+  return launch_result();
 }
 
 cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* out, cudaStream_t s) {
@@ -295,17 +310,19 @@ cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* ou
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fold_point_kernel, (const float*)h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W,
-                            muref, (const double*)h->d_n64, (const double*)h->d_b64,
-                            (const unsigned char*)h->d_mask, (const double*)h->d_cdata, (float*)nullptr,
-                            (float*)nullptr, h->d_part, h->d_ticket, out, h->d_status);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fold_point_kernel, (const float*)h->d_R, h->n_rec, h->ld_r,
+                                           gv_rows_per_block(h), W, muref, (const double*)h->d_n64,
+                                           (const double*)h->d_b64, (const unsigned char*)h->d_mask,
+                                           (const double*)h->d_cdata, (float*)nullptr, (float*)nullptr, h->d_part,
+                                           h->d_ticket, out, h->d_status, inject_timeout());
+  return e != cudaSuccess ? e : launch_result();
 }
 
 cudaError_t launch_reduce_parts(const srw_ctx* h, const double* parts, int n_parts, int P, double* out,
                                 cudaStream_t s) {
   const int thr = 256;
   reduce_parts_kernel<<<(P + thr - 1) / thr, thr, 0, s>>>(parts, n_parts, P, h->d_cdata, out, h->d_status);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStream_t s) {
@@ -319,7 +336,7 @@ cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s) {
   const int thr = 256;
   data_ref_kernel<<<(h->n_rec + thr - 1) / thr, thr, 0, s>>>(h->d_n64, h->d_b64, h->d_muref64, h->d_mask, h->n_rec,
                                                              h->d_rinv, h->d_bref64, h->d_nbm, h->d_nb2, h->d_nb4);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_result();
   if (e == cudaSuccess && h->d_lin) e = launch_linear_consts(h, s);
   return e;
 }
@@ -334,7 +351,7 @@ __global__ void add_ref_kernel(float* __restrict__ out, const double* __restrict
 cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s) {
   const size_t n = (size_t)P * h->n_rec;
   add_ref_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, h->d_muref64, P, h->n_rec);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 }  // namespace srw
@@ -431,8 +448,9 @@ extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld
   }
   cdata_kernel<<<1, 1024, 0, s>>>(counts, mask, n_rec, &sc->c_data);
   fold_point_kernel<<<grid, kGvThreads, smem, s>>>(R, n_rec, ld, rpb, W, nullptr, counts, bkg, mask, &sc->c_data,
-                                                    nullptr, nullptr, sc->parts, &sc->ticket, out, &sc->status);
-  if ((e = cudaGetLastError()) != cudaSuccess) {
+                                                    nullptr, nullptr, sc->parts, &sc->ticket, out, &sc->status,
+                                                    inject_timeout());
+  if ((e = launch_result()) != cudaSuccess) {
     g_noalloc_err = cudaGetErrorString(e);
     return SRW_ECUDA;
   }

@@ -324,18 +324,18 @@ cudaError_t launch_linear_profiled(const srw_ctx* h, const float* theta, int P, 
   linear_profiled_kernel<<<grid, kLinThreads, 0, s>>>(theta, P, df_from_double(h->sin2w), h->cref, h->d_lin,
                                                        h->d_linp, h->n_rec, inv_var, h->d_cdata, out, alpha,
                                                        h->d_status);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s) {
   linear_m_kernel<<<h->n_rec, 256, 0, s>>>(h->d_R, h->ld_r, h->n_t, h->d_basis, h->d_ssm64, h->d_esm64, h->d_linM);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_linear_consts(srw_ctx* h, cudaStream_t s) {
   linear_consts_kernel<<<(h->n_rec + 255) / 256, 256, 0, s>>>(h->d_linM, h->d_n64, h->d_bref64, h->d_muref64, h->d_mask,
                                                              h->n_rec, h->d_lin, h->d_linp);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_linear_loglik(const srw_ctx* h, const float* theta, int P, double* out, double* grad,
@@ -347,7 +347,7 @@ cudaError_t launch_linear_loglik(const srw_ctx* h, const float* theta, int P, do
   else
     linear_loglik_kernel<false><<<grid, kLinThreads, 0, s>>>(theta, P, df_from_double(h->sin2w), h->cref, h->d_lin,
                                                              h->n_rec, h->d_cdata, out, nullptr, h->d_status);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 }  // namespace srw

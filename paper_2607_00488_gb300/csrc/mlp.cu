@@ -21,11 +21,13 @@
 // Activations are stored both row-major (operand A of the next layer's
 // product) and transposed (operand of the weight-gradient product), so every
 // product reads K-major operands.  Roles of a CTA: warp 0 TMA producer, warp 1
-// MMA issuer / TMEM owner, warps 2-5 epilogue (warp w reads TMEM lanes
-// 32 (w % 4) ...).  Every wait is bounded; a timeout raises kStatusTimeout.
+// MMA issuer / TMEM owner, warps 2-9 epilogue: two per TMEM lane quarter
+// (warp w reads lanes 32 (w % 4) ...), each on half the columns.  Every wait
+// is bounded; a timeout raises kStatusTimeout.
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -419,6 +421,9 @@ __global__ void log_counts_kernel(const float* __restrict__ src, long long rows,
 }
 
 // Per-column sums and sums of squares (FP64) over rows, for the standardization.
+// Column sums and sums of squares of one block of 4096 rows, written to the
+// block's own slot (no atomics: the statistics, and so every resumed fit, are
+// the same bit for bit whatever the order in which the blocks run).
 __global__ void colstats_kernel(const float* __restrict__ t, long long rows, int ld, int n, double* __restrict__ s1,
                                 double* __restrict__ s2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -430,16 +435,21 @@ __global__ void colstats_kernel(const float* __restrict__ t, long long rows, int
     a += x;
     b += x * x;
   }
-  atomicAdd(s1 + j, a);
-  atomicAdd(s2 + j, b);
+  s1[(size_t)blockIdx.y * n + j] = a;
+  s2[(size_t)blockIdx.y * n + j] = b;
 }
 
-__global__ void finish_stats_kernel(const double* __restrict__ s1, const double* __restrict__ s2, long long rows,
-                                    int n, float* __restrict__ mean, float* __restrict__ stdv) {
+__global__ void finish_stats_kernel(const double* __restrict__ s1, const double* __restrict__ s2, int n_blocks,
+                                    long long rows, int n, float* __restrict__ mean, float* __restrict__ stdv) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const double m = s1[j] / (double)rows;
-  const double var = fmax(s2[j] / (double)rows - m * m, 0.0);
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < n_blocks; ++k) {  // fixed order over the row blocks
+    a += s1[(size_t)k * n + j];
+    b += s2[(size_t)k * n + j];
+  }
+  const double m = a / (double)rows;
+  const double var = fmax(b / (double)rows - m * m, 0.0);
   const double s = sqrt(var);
   mean[j] = (float)m;
   stdv[j] = s > 1e-12 ? (float)s : 1.f;
@@ -640,7 +650,7 @@ cudaError_t launch_mode(const Gemm& g, int sm_count, unsigned* status, cudaStrea
   const int tiles = (g.M / kBM) * (g.N / BN);
   const int grid = tiles < sm_count ? tiles : sm_count;
   mlp_gemm_kernel<BN, MODE><<<grid, kGemmThreads, GemmShape<BN>::kSmem, s>>>(g.ma, g.mb, g.M, g.N, g.K, g.E, status);
-  return cudaGetLastError();
+  return srw::launch_result();
 }
 
 cudaError_t run_gemm(const Gemm& g, int sm_count, unsigned* status, cudaStream_t s) {
@@ -714,6 +724,7 @@ struct srw_surrogate_ctx {
   float4* binc = nullptr;  // per-bin constants of the scan epilogue
   int stats_ready = 0;
   long long adam_t = 0;
+  long long epochs_done = 0;  // completed epochs of the last (resumable) fit
   unsigned* d_status = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<SurrogateBatch*> batches;
@@ -738,7 +749,7 @@ srw_status scuda(srw_surrogate s, cudaError_t e, const char* what) {
 
 template <class T>
 cudaError_t salloc(T** p, size_t n) {
-  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
+  return srw::dev_malloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
 }
 template <class T>
 void sfree(T*& p) {
@@ -897,7 +908,7 @@ cudaError_t launch_input(srw_surrogate s, const float* theta, int rows, Surrogat
   const float4 h0 = make_float4(s->half[0], s->half[1], s->half[2], s->half[3]);
   srw::mlp_input_kernel<<<(B->M + 255) / 256, 256, 0, st>>>(theta, rows, B->M, c0, s->centre[4], h0, s->half[4], B->x,
                                                             B->train ? B->xt : nullptr);
-  return cudaGetLastError();
+  return srw::launch_result();
 }
 
 // Forward through the hidden layers (rows of theta; B->M >= rows).
@@ -935,7 +946,7 @@ cudaError_t fit_pass(srw_surrogate s, const float* theta, const float* targets, 
     const __nv_bfloat16* dzt = l == 3 ? B->dyt : B->dzt[l];
     if (e == cudaSuccess) {
       srw::rowsum_kernel<<<(s->L[l].out + 7) / 8, 256, 0, st>>>(dzt, s->L[l].out, B->M, s->L[l].gb);
-      e = cudaGetLastError();
+      e = srw::launch_result();
     }
     if (l > 0 && e == cudaSuccess) e = srw::run_gemm(B->bwd[l - 1], s->sm_count, s->d_status, st);
   }
@@ -963,7 +974,7 @@ cudaError_t adam_update(srw_surrogate s, float lr, float beta1, float beta2, flo
   A.c1 = (float)(1.0 - std::pow((double)beta1, (double)s->adam_t));
   A.c2 = (float)(1.0 - std::pow((double)beta2, (double)s->adam_t));
   srw::adam_kernel<<<(unsigned)((off + 255) / 256), 256, 0, st>>>(A);
-  return cudaGetLastError();
+  return srw::launch_result();
 }
 
 constexpr int kScanChunk = 1 << 20;  // points per surrogate launch chain in scans
@@ -987,7 +998,7 @@ srw_status loglik_device(srw_surrogate s, const float* theta, long long P, T* ou
     if (e == cudaSuccess) {
       srw::scan_reduce_kernel<T><<<(rows + 255) / 256, 256, 0, st>>>(B->parts, s->n_out_pad / 256 * 2, rows, s->h->d_cdata,
                                                                    out + off);
-      e = cudaGetLastError();
+      e = srw::launch_result();
     }
     if (e != cudaSuccess) return scuda(s, e, "surrogate likelihood");
   }
@@ -1030,7 +1041,7 @@ srw_status upload_weights(srw_surrogate s, const float* const* w) {
     S_CUDA(s, cudaMemset(L.mb, 0, sizeof(float) * L.out), "adam state");
     S_CUDA(s, cudaMemset(L.vb, 0, sizeof(float) * L.out), "adam state");
     srw::cast_weights_kernel<<<(unsigned)((W.size() + 255) / 256), 256, 0, s->stream>>>(L.w, L.out, L.in, L.w_bf, L.wt_bf);
-    S_CUDA(s, cudaGetLastError(), "cast weights");
+    S_CUDA(s, srw::launch_result(), "cast weights");
   }
   s->adam_t = 0;
   S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
@@ -1145,7 +1156,7 @@ srw_status srw_surrogate_forward(srw_surrogate s, const float* theta, int P, flo
   srw_status st = get_batch(s, M, false, &B);
   if (st != SRW_OK) return st;
   float* d_th = nullptr;
-  S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   cudaError_t e = cudaSuccess;
   if (!B->y) {  // the FP32 output buffer exists only for this hook
@@ -1174,8 +1185,8 @@ srw_status srw_surrogate_gradients(srw_surrogate s, const float* theta, const fl
   srw_status st = get_batch(s, M, true, &B);
   if (st != SRW_OK) return st;
   float *d_th = nullptr, *d_t = nullptr;
-  S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
-  S_CUDA(s, cudaMallocAsync(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
   S_CUDA(s, cudaMemsetAsync(d_t, 0, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "zero");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   S_CUDA(s, cudaMemcpy2DAsync(d_t, sizeof(float) * s->n_out_pad, targets, sizeof(float) * s->n_out,
@@ -1215,8 +1226,8 @@ srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const f
   srw_status st = get_batch(s, M, true, &B);
   if (st != SRW_OK) return st;
   float *d_th = nullptr, *d_t = nullptr;
-  S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
-  S_CUDA(s, cudaMallocAsync(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
   S_CUDA(s, cudaMemsetAsync(d_t, 0, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "zero");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   S_CUDA(s, cudaMemcpy2DAsync(d_t, sizeof(float) * s->n_out_pad, targets, sizeof(float) * s->n_out,
@@ -1234,9 +1245,12 @@ srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const f
   return check_status(s, s->stream);
 }
 
-srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* o,
-                             float* epoch_loss) {
+static srw_status fit_impl(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* o, int first_epoch,
+                           int stop_epoch, const char* checkpoint_path, float* epoch_loss) {
   if (!s || !theta || !o || n < 1) return SRW_EINVAL;
+  if (stop_epoch <= 0) stop_epoch = o->epochs;
+  if (first_epoch < 0 || stop_epoch > o->epochs || first_epoch > stop_epoch)
+    return sfail(s, SRW_EINVAL, "need 0 <= first_epoch <= stop_epoch <= epochs");
   if (o->batch < srw::kBM || o->batch % srw::kBM || o->epochs < 0 || !(o->lr > 0.f) || !(o->lr_final >= 0.f))
     return sfail(s, SRW_EINVAL, "batch must be a positive multiple of 128; epochs >= 0; lr > 0");
   if (o->precision < SRW_FP32 || o->precision > SRW_FP16X3) return sfail(s, SRW_EINVAL, "bad precision");
@@ -1259,10 +1273,10 @@ srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, c
   cudaError_t e = salloc(&d_th, (size_t)n_pad * 5);
   if (e == cudaSuccess) e = salloc(&d_t, (size_t)n_pad * NO);
   if (e == cudaSuccess) e = salloc(&d_tmp, (size_t)kGen * NR);
-  if (e == cudaSuccess) e = salloc(&d_stats, 2 * (size_t)NO);
+  const int n_sblocks = (int)((n + 4095) / 4096);
+  if (e == cudaSuccess) e = salloc(&d_stats, 2 * (size_t)NR * n_sblocks);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_th, 0, sizeof(float) * n_pad * 5, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_t, 0, sizeof(float) * n_pad * NO, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_stats, 0, sizeof(double) * 2 * NO, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_th, theta, sizeof(float) * n * 5, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     cleanup();
@@ -1280,11 +1294,12 @@ srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, c
                                                                                       d_t + off * NO);
   }
   // per-bin standardization over the training set
-  srw::colstats_kernel<<<dim3((NR + 255) / 256, (unsigned)((n + 4095) / 4096)), 256, 0, st>>>(d_t, n, NO, NR, d_stats,
-                                                                                          d_stats + NO);
-  srw::finish_stats_kernel<<<(NR + 255) / 256, 256, 0, st>>>(d_stats, d_stats + NO, n, NR, s->mean, s->stdv);
+  srw::colstats_kernel<<<dim3((NR + 255) / 256, (unsigned)n_sblocks), 256, 0, st>>>(
+      d_t, n, NO, NR, d_stats, d_stats + (size_t)NR * n_sblocks);
+  srw::finish_stats_kernel<<<(NR + 255) / 256, 256, 0, st>>>(d_stats, d_stats + (size_t)NR * n_sblocks, n_sblocks, n,
+                                                             NR, s->mean, s->stdv);
   srw::standardize_kernel<<<(unsigned)((n * NO + 255) / 256), 256, 0, st>>>(d_t, n, NO, NR, s->mean, s->stdv);
-  if ((e = cudaGetLastError()) != cudaSuccess) {
+  if ((e = srw::launch_result()) != cudaSuccess) {
     cleanup();
     return scuda(s, e, "targets");
   }
@@ -1295,8 +1310,8 @@ srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, c
     return r;
   }
   const long long total = steps * o->epochs;
-  long long t = 0;
-  for (int ep = 0; ep < o->epochs; ++ep) {
+  long long t = steps * first_epoch;  // a resumed fit continues the learning-rate schedule
+  for (int ep = first_epoch; ep < stop_epoch; ++ep) {
     e = cudaMemsetAsync(B->loss, 0, sizeof(double), st);
     for (long long b = 0; b < steps && e == cudaSuccess; ++b, ++t) {
       const int rows = (int)std::min<long long>(M, n - b * M);
@@ -1314,10 +1329,30 @@ srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, c
     }
     // each step's error is already a mean over its own points: average the steps
     if (epoch_loss) epoch_loss[ep] = (float)(sse / ((double)n * NR));
+    s->epochs_done = ep + 1;
+    s->stats_ready = 1;
+    if (checkpoint_path) {
+      const srw_status cr = srw_surrogate_save(s, checkpoint_path);
+      if (cr != SRW_OK) {
+        cleanup();
+        return cr;
+      }
+    }
   }
   cleanup();
   s->stats_ready = 1;
   return check_status(s, st);
+}
+
+srw_status srw_surrogate_fit(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* o,
+                             float* epoch_loss) {
+  if (s) s->epochs_done = 0;
+  return fit_impl(s, theta, n, o, 0, 0, nullptr, epoch_loss);
+}
+
+srw_status srw_surrogate_fit_resume(srw_surrogate s, const float* theta, long long n, const srw_fit_opts* o,
+                                    int first_epoch, int stop_epoch, const char* checkpoint_path, float* epoch_loss) {
+  return fit_impl(s, theta, n, o, first_epoch, stop_epoch, checkpoint_path, epoch_loss);
 }
 
 srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, double* out, int where, void* stream) {
@@ -1333,8 +1368,8 @@ srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, doub
     if (!std::isfinite(theta[q])) return sfail(s, SRW_EINVAL, "theta must be finite");
   float* d_th = nullptr;
   double* d_out = nullptr;
-  S_CUDA(s, cudaMallocAsync(&d_th, sizeof(float) * 5 * (size_t)P, st), "alloc");
-  S_CUDA(s, cudaMallocAsync(&d_out, sizeof(double) * (size_t)P, st), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, st), "alloc");
+  S_CUDA(s, srw::dev_malloc_async(&d_out, sizeof(double) * (size_t)P, st), "alloc");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, st), "upload");
   srw_status r = loglik_device<double>(s, d_th, P, d_out, st);
   if (r == SRW_OK)
@@ -1662,6 +1697,286 @@ srw_status srw_surrogate_get_standardization(srw_surrogate s, float* mean, float
   S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
   S_CUDA(s, cudaMemcpy(mean, s->mean, sizeof(float) * s->n_out, cudaMemcpyDeviceToHost), "read");
   S_CUDA(s, cudaMemcpy(stdv, s->stdv, sizeof(float) * s->n_out, cudaMemcpyDeviceToHost), "read");
+  return SRW_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the whole training state (FP32 master weights and biases, Adam
+// first and second moments and step count, the per-bin standardization and
+// the completed epochs), written to `path + ".tmp"` and renamed over `path`,
+// so that a crash leaves either the previous or the new checkpoint.  Binary,
+// little-endian, with a 64-bit FNV-1a checksum of the payload.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, n_out, n_out_pad, stats_ready;
+  int64_t adam_t, epochs_done;
+  float centre[5], half[5];
+  int32_t out[4], in[4];
+  uint64_t payload_bytes, checksum;
+};
+constexpr char kCkptMagic[8] = {'S', 'R', 'W', 'C', 'K', 'P', 'T', '1'};
+
+uint64_t fnv1a(const std::vector<unsigned char>& b) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : b) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// The device arrays of the training state in file order, with their lengths.
+std::vector<std::pair<float*, size_t>> state_arrays(srw_surrogate s) {
+  std::vector<std::pair<float*, size_t>> a;
+  for (SurrogateLayer& L : s->L) {
+    const size_t nw = (size_t)L.out * L.in;
+    a.push_back({L.w, nw});
+    a.push_back({L.b, (size_t)L.out});
+    a.push_back({L.mw, nw});
+    a.push_back({L.vw, nw});
+    a.push_back({L.mb, (size_t)L.out});
+    a.push_back({L.vb, (size_t)L.out});
+  }
+  a.push_back({s->mean, (size_t)s->n_out_pad});
+  a.push_back({s->stdv, (size_t)s->n_out_pad});
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+srw_status srw_surrogate_save(srw_surrogate s, const char* path) {
+  if (!s || !path) return SRW_EINVAL;
+  S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.n_out = s->n_out;
+  hd.n_out_pad = s->n_out_pad;
+  hd.stats_ready = s->stats_ready;
+  hd.adam_t = s->adam_t;
+  hd.epochs_done = s->epochs_done;
+  for (int k = 0; k < 5; ++k) {
+    hd.centre[k] = s->centre[k];
+    hd.half[k] = s->half[k];
+  }
+  for (int l = 0; l < 4; ++l) {
+    hd.out[l] = s->L[l].out;
+    hd.in[l] = s->L[l].in;
+  }
+  std::vector<unsigned char> payload;
+  for (auto& a : state_arrays(s)) {
+    const size_t off = payload.size();
+    payload.resize(off + a.second * sizeof(float));
+    S_CUDA(s, cudaMemcpy(payload.data() + off, a.first, a.second * sizeof(float), cudaMemcpyDeviceToHost), "read state");
+  }
+  hd.payload_bytes = payload.size();
+  hd.checksum = fnv1a(payload);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return sfail(s, SRW_EINVAL, "cannot write checkpoint " + tmp);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                  std::fwrite(payload.data(), 1, payload.size(), f) == payload.size() && std::fflush(f) == 0;
+  if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return sfail(s, SRW_EINVAL, std::string("cannot write checkpoint ") + path);
+  }
+  return SRW_OK;
+}
+
+srw_status srw_surrogate_load(srw_surrogate s, const char* path, long long* epochs_done) {
+  if (!s || !path) return SRW_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return sfail(s, SRW_EINVAL, std::string("cannot read checkpoint ") + path);
+  CkptHeader hd;
+  std::vector<unsigned char> payload;
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kCkptMagic, 8) == 0 && hd.version == 1;
+  if (ok && hd.payload_bytes < ((uint64_t)1 << 34)) {
+    payload.resize(hd.payload_bytes);
+    ok = std::fread(payload.data(), 1, payload.size(), f) == payload.size();
+  } else {
+    ok = false;
+  }
+  std::fclose(f);
+  if (!ok) return sfail(s, SRW_EINVAL, std::string("not a surrogate checkpoint: ") + path);
+  if (fnv1a(payload) != hd.checksum) return sfail(s, SRW_EINVAL, std::string("checkpoint checksum mismatch: ") + path);
+  bool same = hd.n_out == s->n_out && hd.n_out_pad == s->n_out_pad;
+  for (int l = 0; l < 4; ++l) same = same && hd.out[l] == s->L[l].out && hd.in[l] == s->L[l].in;
+  for (int k = 0; k < 5; ++k) same = same && hd.centre[k] == s->centre[k] && hd.half[k] == s->half[k];
+  if (!same) return sfail(s, SRW_EINVAL, "checkpoint of a different network or parameter box");
+  size_t want = 0;
+  for (auto& a : state_arrays(s)) want += a.second * sizeof(float);
+  if (want != payload.size()) return sfail(s, SRW_EINVAL, "checkpoint size does not match the network");
+  S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
+  size_t off = 0;
+  for (auto& a : state_arrays(s)) {
+    S_CUDA(s, cudaMemcpy(a.first, payload.data() + off, a.second * sizeof(float), cudaMemcpyHostToDevice), "upload state");
+    off += a.second * sizeof(float);
+  }
+  for (SurrogateLayer& L : s->L)
+    srw::cast_weights_kernel<<<(unsigned)(((size_t)L.out * L.in + 255) / 256), 256, 0, s->stream>>>(L.w, L.out, L.in,
+                                                                                                  L.w_bf, L.wt_bf);
+  S_CUDA(s, srw::launch_result(), "cast weights");
+  S_CUDA(s, cudaStreamSynchronize(s->stream), "sync");
+  s->adam_t = hd.adam_t;
+  s->epochs_done = hd.epochs_done;
+  s->stats_ready = hd.stats_ready;
+  if (epochs_done) *epochs_done = hd.epochs_done;
+  return SRW_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Resumable scans: a scan of n points cut into chunks of chunk_points
+// consecutive Sobol indices, each chunk an independent srw_surrogate_scan; a
+// state file records every completed chunk's result (rewritten through a
+// temporary file and a rename after each chunk), so a scan that stops, for
+// any reason, continues from its last completed chunk.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::string scan_key(const srw_scan_opts* o, long long chunk) {
+  std::vector<unsigned char> b((size_t)o->n_check * 5 * sizeof(float));
+  if (o->n_check > 0) std::memcpy(b.data(), o->check_theta, b.size());
+  char k[512];
+  std::snprintf(k, sizeof(k),
+                "srw-scan 1 first=%lld n=%lld chunk=%lld keep=%.17g tol=%.17g cells=%d prec=%d rule=%d margin=%.17g "
+                "check=%d hash=%016llx",
+                o->first, o->n_points, chunk, o->keep_frac, o->tol, o->cells_per_dim, o->precision, o->rule,
+                o->margin_factor, o->n_check, (unsigned long long)fnv1a(b));
+  return k;
+}
+
+struct ChunkRecord {
+  long long c;
+  srw_scan_result r;
+};
+
+// 0: read (or no file); 1: the file belongs to another scan; 2: unreadable
+int read_scan_state(const char* path, const std::string& key, std::vector<ChunkRecord>& recs) {
+  recs.clear();
+  FILE* f = std::fopen(path, "r");
+  if (!f) return 0;
+  char line[1024];
+  int st = 0;
+  if (!std::fgets(line, sizeof(line), f) || key != std::string(line).substr(0, std::string(line).find('\n'))) st = 1;
+  while (st == 0 && std::fgets(line, sizeof(line), f)) {
+    ChunkRecord q;
+    std::memset(&q, 0, sizeof(q));
+    srw_scan_result& r = q.r;
+    const int n = std::sscanf(line, "chunk %lld %lg %lld %g %g %g %g %g %lg %lld %lld %lld %d %d %lg %g %g %g %g", &q.c,
+                              &r.best_value, &r.best_index, &r.best_theta[0], &r.best_theta[1], &r.best_theta[2],
+                              &r.best_theta[3], &r.best_theta[4], &r.surrogate_min, &r.n_kept, &r.n_selected,
+                              &r.n_rescued, &r.n_cells, &r.n_flagged_cells, &r.check_max_abs_d, &r.ms_check,
+                              &r.ms_surrogate, &r.ms_select, &r.ms_exact);
+    if (n != 19) {
+      st = 2;
+      break;
+    }
+    recs.push_back(q);
+  }
+  std::fclose(f);
+  return st;
+}
+
+bool write_scan_state(const char* path, const std::string& key, const std::vector<ChunkRecord>& recs) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  bool ok = std::fprintf(f, "%s\n", key.c_str()) > 0;
+  for (const ChunkRecord& q : recs) {
+    const srw_scan_result& r = q.r;
+    ok = ok && std::fprintf(f, "chunk %lld %.17g %lld %.9g %.9g %.9g %.9g %.9g %.17g %lld %lld %lld %d %d %.17g %.9g %.9g "
+                               "%.9g %.9g\n",
+                            q.c, r.best_value, r.best_index, r.best_theta[0], r.best_theta[1], r.best_theta[2],
+                            r.best_theta[3], r.best_theta[4], r.surrogate_min, r.n_kept, r.n_selected, r.n_rescued,
+                            r.n_cells, r.n_flagged_cells, r.check_max_abs_d, r.ms_check, r.ms_surrogate, r.ms_select,
+                            r.ms_exact) > 0;
+  }
+  ok = std::fflush(f) == 0 && ok;
+  if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return false;
+  }
+  return true;
+}
+
+// The scan's result from its chunks': the smallest exact minimum (ties: the
+// smaller Sobol index), counts and times summed.
+void merge_chunks(const std::vector<ChunkRecord>& recs, srw_scan_result* res) {
+  std::memset(res, 0, sizeof(*res));
+  res->best_value = INFINITY;
+  res->best_index = -1;
+  res->surrogate_min = INFINITY;
+  for (const ChunkRecord& q : recs) {
+    const srw_scan_result& r = q.r;
+    if (r.best_index >= 0 && (r.best_value < res->best_value ||
+                              (r.best_value == res->best_value && r.best_index < res->best_index))) {
+      res->best_value = r.best_value;
+      res->best_index = r.best_index;
+      std::memcpy(res->best_theta, r.best_theta, sizeof(r.best_theta));
+    }
+    res->surrogate_min = std::min(res->surrogate_min, r.surrogate_min);
+    res->n_kept += r.n_kept;
+    res->n_selected += r.n_selected;
+    res->n_rescued += r.n_rescued;
+    res->n_cells = r.n_cells;
+    res->n_flagged_cells = r.n_flagged_cells;
+    res->check_max_abs_d = std::max(res->check_max_abs_d, r.check_max_abs_d);
+    res->ms_check += r.ms_check;
+    res->ms_surrogate += r.ms_surrogate;
+    res->ms_select += r.ms_select;
+    res->ms_exact += r.ms_exact;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+srw_status srw_surrogate_scan_chunked(srw_surrogate s, const srw_scan_opts* o, long long chunk_points,
+                                      const char* state_path, int max_new_chunks, srw_scan_result* res,
+                                      int* complete) {
+  if (!s || !o || !res || !state_path || chunk_points < 1) return SRW_EINVAL;
+  if (complete) *complete = 0;
+  if (o->n_points < 1 || o->first < 0) return sfail(s, SRW_EINVAL, "bad scan options");
+  const std::string key = scan_key(o, chunk_points);
+  std::vector<ChunkRecord> recs;
+  const int rs = read_scan_state(state_path, key, recs);
+  if (rs == 1) return sfail(s, SRW_EINVAL, "the state file belongs to a different scan");
+  if (rs == 2) return sfail(s, SRW_EINVAL, "the state file is damaged");
+  const long long n_chunks = (o->n_points + chunk_points - 1) / chunk_points;
+  std::vector<char> done((size_t)n_chunks, 0);
+  for (const ChunkRecord& q : recs)
+    if (q.c >= 0 && q.c < n_chunks) done[(size_t)q.c] = 1;
+  int fresh = 0;
+  for (long long c = 0; c < n_chunks; ++c) {
+    if (done[(size_t)c]) continue;
+    if (max_new_chunks > 0 && fresh >= max_new_chunks) break;
+    srw_scan_opts oc = *o;
+    oc.first = o->first + c * chunk_points;
+    oc.n_points = std::min(chunk_points, o->n_points - c * chunk_points);
+    ChunkRecord q;
+    q.c = c;
+    const srw_status st = srw_surrogate_scan(s, &oc, &q.r);
+    if (st != SRW_OK) return st;
+    recs.push_back(q);
+    done[(size_t)c] = 1;
+    ++fresh;
+    if (!write_scan_state(state_path, key, recs)) return sfail(s, SRW_EINVAL, "cannot write the scan state file");
+  }
+  merge_chunks(recs, res);
+  bool all = true;
+  for (char d : done) all = all && d;
+  if (complete) *complete = all ? 1 : 0;
   return SRW_OK;
 }
 

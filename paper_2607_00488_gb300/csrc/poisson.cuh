@@ -45,4 +45,25 @@ __device__ __forceinline__ float poisson_term_f32_tc(float mu, float n) {
   return fabsf(v) < 0.1f ? ts : tl;
 }
 
+// The same term from dm = mu - n (and n), for callers that form mu - n
+// directly: an FP32 mu of 1e5 counts carries an absolute rounding error of
+// ~6e-3, while mu - n near the data is a few hundred, so its FP32 value is
+// ~1e3 times more precise and the series branch then loses nothing to it.
+// The log branch (far from the data) takes mu - n of the same rounded mu that
+// enters the logarithm: then mu's rounding error e enters t only as
+// (1 - n/mu) e, as in the exact expression (dt/dmu = 1 - n/mu); with the
+// unrounded dm it would enter as -(n/mu) e, about e itself.
+// Same branches, floor and special cases as poisson_term_f32_tc.
+__device__ __forceinline__ float poisson_term_f32_dm(float dm, float n) {
+  const float mu = n + dm, s = n + mu;
+  const float v = __fdividef(-dm, s);
+  const float v2 = v * v;
+  float p = fmaf(v2, 1.f / 9.f, 1.f / 7.f);
+  p = fmaf(v2, p, 1.f / 5.f);
+  p = fmaf(v2, p, 1.f / 3.f);
+  const float ts = fmaf(-dm, v, 2.f * n * v * v2 * p);
+  const float tl = fmaf(n, logf(fmaxf(__fdividef(n, mu), 1e-30f)), mu - n);
+  return fabsf(v) < 0.1f ? ts : tl;
+}
+
 }  // namespace srw

@@ -423,25 +423,25 @@ __global__ void muref_kernel(const float* __restrict__ R, int ld, int n_t, const
 
 cudaError_t launch_reference_fold(srw_ctx* h, cudaStream_t s) {
   double* d_w = nullptr;
-  cudaError_t e = cudaMallocAsync(&d_w, sizeof(double) * h->n_t, s);
+  cudaError_t e = dev_malloc_async(&d_w, sizeof(double) * h->n_t, s);
   if (e != cudaSuccess) return e;
   wref_kernel<<<(h->n_t + 255) / 256, 256, 0, s>>>(h->d_basis, h->d_ssm64, h->d_esm64, h->n_t, h->cref, d_w);
   muref_kernel<<<h->n_rec, 256, 0, s>>>(h->d_R, h->ld_r, h->n_t, d_w, h->d_muref64);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_result()) != cudaSuccess) return e;
   return cudaFreeAsync(d_w, s);
 }
 
 cudaError_t launch_weights_from_basis(const srw_ctx* h, const float* theta, float* W, cudaStream_t s) {
   weights_from_basis_kernel<<<(h->k_pad + 255) / 256, 256, 0, s>>>(theta, df_from_double(h->sin2w), h->cref,
                                                                   h->d_shat, h->d_shat_lo, h->k_pad, W);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_basis_fp64(const srw_ctx* h, cudaStream_t s) {
   const ModelView m = model_view(h);
   const double gl_mu = -0.5 + h->sin2w, gr_mu = h->sin2w;
   basis_fp64_kernel<<<h->n_t, kBasisThreads, 0, s>>>(m, gl_mu, gr_mu, h->kappa, h->d_basis);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 cudaError_t launch_spectrum_point(const srw_ctx* h, const float* theta, float* S_out, float* W_out, float* ssm_out,
@@ -456,7 +456,7 @@ cudaError_t launch_spectrum_point(const srw_ctx* h, const float* theta, float* S
   delta = delta && h->use_ref;
   spectrum_point_kernel<<<grid, kSpecThreads, 0, s>>>(m, theta, df_from_double(h->sin2w), df_from_double(h->kappa),
                                                         g, delta ? 1 : 0, S_out, W_out, ssm_out);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 // Builds S_SM (FP64), lambda, E_SM and shat.  Requires d_basis.
@@ -465,24 +465,24 @@ cudaError_t launch_build_shat(srw_ctx* h, cudaStream_t s) {
   const int g_t = (n_t + thr - 1) / thr;
   const double s2 = h->sin2w;
   ssm_from_basis_kernel<<<g_t, thr, 0, s>>>(h->d_basis, n_t, 0.5 + s2, s2, -0.5 + s2, s2, h->d_ssm64);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_result();
   if (e != cudaSuccess) return e;
   if (!h->has_esm_input) {
     double* d_eff = nullptr;
     double* d_lam = nullptr;
-    if ((e = cudaMallocAsync(&d_eff, sizeof(double) * (n_t + 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc_async(&d_eff, sizeof(double) * (n_t + 1), s)) != cudaSuccess) return e;
     d_lam = d_eff + n_t;
     efficiency_kernel<<<g_t, thr, 0, s>>>(h->d_R, h->n_rec, h->ld_r, n_t, d_eff);
     lambda_kernel<<<1, 1024, 0, s>>>(d_eff, h->d_ssm64, n_t, h->exposure, d_lam);
     esm_kernel<<<g_t, thr, 0, s>>>(h->d_ssm64, d_lam, n_t, h->d_esm64);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_result()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(&h->lambda, d_lam, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
     if ((e = cudaFreeAsync(d_eff, s)) != cudaSuccess) return e;
   }
   const int g_k = (h->k_pad + thr - 1) / thr;
   shat_kernel<<<g_k, thr, 0, s>>>(h->d_basis, h->d_ssm64, h->d_esm64, n_t, h->k_pad, h->d_shat, h->d_shat_lo,
                                     h->d_esm32);
-  return cudaGetLastError();
+  return launch_result();
 }
 
 }  // namespace srw

@@ -66,7 +66,7 @@ DataView data_view(const srw_ctx* h) {
 
 template <class T>
 static cudaError_t dalloc(srw_ctx* h, T** p, size_t n) {
-  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1));
+  cudaError_t e = dev_malloc((void**)p, sizeof(T) * std::max<size_t>(n, 1));
   if (e == cudaSuccess) h->device_bytes += sizeof(T) * std::max<size_t>(n, 1);
   return e;
 }
@@ -165,8 +165,8 @@ static srw_status ensure_staging(srw_ctx* h, int P) {
   destroy_graphs(h);
   dfree(h->d_theta);
   dfree(h->d_out);
-  SRW_CUDA(h, cudaMalloc(&h->d_theta, sizeof(float) * 5 * (size_t)cap), "staging theta");
-  SRW_CUDA(h, cudaMalloc(&h->d_out, sizeof(double) * (size_t)cap), "staging out");
+  SRW_CUDA(h, dev_malloc(&h->d_theta, sizeof(float) * 5 * (size_t)cap), "staging theta");
+  SRW_CUDA(h, dev_malloc(&h->d_out, sizeof(double) * (size_t)cap), "staging out");
   h->stage_cap = cap;
   return SRW_OK;
 }
@@ -177,7 +177,7 @@ static srw_status ensure_wscale(srw_ctx* h, int P) {
   const int cap = std::max(P, 2 * h->wscale_cap);
   destroy_graphs(h);
   dfree(h->d_wscale);
-  SRW_CUDA(h, cudaMalloc(&h->d_wscale, sizeof(float) * (size_t)cap), "FP16 scales");
+  SRW_CUDA(h, dev_malloc(&h->d_wscale, sizeof(float) * (size_t)cap), "FP16 scales");
   h->wscale_cap = cap;
   return SRW_OK;
 }
@@ -187,16 +187,31 @@ static srw_status ensure_bparts(srw_ctx* h, size_t n) {
   size_t cap = std::max(n, 2 * h->bpart_cap);
   destroy_graphs(h);
   dfree(h->d_bpart);
-  SRW_CUDA(h, cudaMalloc(&h->d_bpart, sizeof(double) * cap), "batched partials");
+  // the debug build keeps canary doubles after the buffer (checked by host-pointer calls)
+  const size_t extra = kDebugChecks ? kCanaryDoubles : 0;
+  SRW_CUDA(h, dev_malloc(&h->d_bpart, sizeof(double) * (cap + extra)), "batched partials");
   h->bpart_cap = cap;
+  if (kDebugChecks) {
+    std::vector<unsigned long long> c(kCanaryDoubles, kCanaryBits);
+    SRW_CUDA(h, cudaMemcpy(h->d_bpart + cap, c.data(), sizeof(double) * kCanaryDoubles, cudaMemcpyHostToDevice),
+             "canary");
+  }
   return SRW_OK;
 }
 
 static srw_status check_status_word(srw_ctx* h, cudaStream_t s, bool* domain) {
   unsigned st = 0;
+  unsigned long long canary[kCanaryDoubles];
   SRW_CUDA(h, cudaMemcpyAsync(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "status read");
+  if (kDebugChecks && h->d_bpart)
+    SRW_CUDA(h, cudaMemcpyAsync(canary, h->d_bpart + h->bpart_cap, sizeof(canary), cudaMemcpyDeviceToHost, s),
+             "canary read");
   SRW_CUDA(h, cudaStreamSynchronize(s), "stream sync");
   if (st) SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
+  if (st & kStatusCheck) return fail(h, SRW_ECHECK, "a debug bounds check failed in a kernel");
+  if (kDebugChecks && h->d_bpart)
+    for (int k = 0; k < kCanaryDoubles; ++k)
+      if (canary[k] != kCanaryBits) return fail(h, SRW_ECHECK, "the canary after the batched partial sums was overwritten");
   if (st & kStatusTimeout) return fail(h, SRW_ETIMEOUT, "a bounded device wait expired; the fold aborted");
   if (domain) *domain = (st & kStatusDomain) != 0;
   return SRW_OK;
@@ -214,6 +229,7 @@ static srw_status run_graph(srw_ctx* h, int path, int precision, int P, const vo
     }
   }
   cudaGraph_t graph = nullptr;
+  fault_take_timeout_fired();  // clear: only an injection inside this capture counts
   SRW_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t eb = body(s);
   cudaError_t ee = cudaStreamEndCapture(s, &graph);
@@ -226,6 +242,14 @@ static srw_status run_graph(srw_ctx* h, int path, int precision, int P, const vo
   cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (ei != cudaSuccess) return cuda_fail(h, ei, "graph instantiate");
+  if (fault_take_timeout_fired()) {
+    // a graph captured with an injected timeout runs once and is not cached
+    // (its destruction is deferred by CUDA until the launch completes)
+    const cudaError_t el = cudaGraphLaunch(exec, s);
+    cudaGraphExecDestroy(exec);
+    if (el != cudaSuccess) return cuda_fail(h, el, "graph launch");
+    return SRW_OK;
+  }
   if (h->graphs.size() >= 32) {
     cudaGraphExecDestroy(h->graphs.front().exec);
     h->graphs.erase(h->graphs.begin());
@@ -461,10 +485,10 @@ static srw_status build_joint(srw_ctx* h, const srw_binning* bin, const srw_sour
   do {                                               \
     if ((e = (call)) != cudaSuccess) return jfail(e, what); \
   } while (0)
-  JT(cudaMalloc(&d_hist, sizeof(double) * cells * n_src), "alloc histograms");
-  JT(cudaMalloc(&d_mask, sizeof(double) * (size_t)n_rec * n_src), "alloc masks");
-  JT(cudaMalloc(&d_live, sizeof(double) * n_rec), "alloc live time");
-  JT(cudaMalloc(&d_col, sizeof(double) * 2 * (size_t)n_t * n_src), "alloc column sums");
+  JT(dev_malloc(&d_hist, sizeof(double) * cells * n_src), "alloc histograms");
+  JT(dev_malloc(&d_mask, sizeof(double) * (size_t)n_rec * n_src), "alloc masks");
+  JT(dev_malloc(&d_live, sizeof(double) * n_rec), "alloc live time");
+  JT(dev_malloc(&d_col, sizeof(double) * 2 * (size_t)n_t * n_src), "alloc column sums");
   std::vector<double> ones(std::max(n_rec, 1), 1.0), live(n_rec, 1.0);
   if (jr->live) std::copy(jr->live, jr->live + n_rec, live.begin());
   JT(cudaMemcpyAsync(d_live, live.data(), sizeof(double) * n_rec, cudaMemcpyHostToDevice, s), "upload live time");
@@ -532,7 +556,7 @@ static srw_status build_joint(srw_ctx* h, const srw_binning* bin, const srw_sour
       h->col_src.push_back(k);
       h->col_bin.push_back(i);
     }
-  JT(cudaMalloc(&d_cols, sizeof(int) * std::max(K, 1)), "alloc columns");
+  JT(dev_malloc(&d_cols, sizeof(int) * std::max(K, 1)), "alloc columns");
   JT(cudaMemcpyAsync(d_cols, all_cols.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s), "upload columns");
   int col0 = 0;
   for (int k = 0; k < n_src; ++k) {
@@ -732,8 +756,8 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
     CREATE_CUDA(tc_prepare(h), "tensor map encode");
     h->tensor_ok = true;
   }
-  h->cfg[0] = FoldConfig{0, 128, 1, 0};
-  h->cfg[1] = h->cfg[2] = h->cfg[3] = tc_num_configs() > 0 ? tc_config(0) : FoldConfig{0, 128, 1, 0};
+  h->cfg[0] = FoldConfig{0, 128, 16, 1, 0};
+  h->cfg[1] = h->cfg[2] = h->cfg[3] = tc_config(0);
   *out = h;
   return SRW_OK;
 #undef CREATE_CUDA
@@ -755,6 +779,7 @@ const char* srw_status_string(srw_status s) {
     case SRW_EDOMAIN: return "expected count <= 0 where data > 0";
     case SRW_ETIMEOUT: return "device wait timed out";
     case SRW_EUNSUPPORTED: return "unsupported device";
+    case SRW_ECHECK: return "debug bounds check failed";
   }
   return "unknown status";
 }
@@ -818,7 +843,7 @@ srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, i
   SRW_CUDA(h, cudaMemcpyAsync(h->d_n64, counts, sizeof(double) * n_rec, cudaMemcpyHostToDevice, s), "upload counts");
   if (mask) SRW_CUDA(h, cudaMemcpyAsync(h->d_mask, mask, n_rec, cudaMemcpyHostToDevice, s), "upload mask");
   if (n_bkg > 0) {
-    SRW_CUDA(h, cudaMallocAsync(&d_bkg, sizeof(double) * (size_t)n_bkg * n_rec, s), "alloc bkg");
+    SRW_CUDA(h, dev_malloc_async(&d_bkg, sizeof(double) * (size_t)n_bkg * n_rec, s), "alloc bkg");
     SRW_CUDA(h, cudaMemcpyAsync(d_bkg, bkg, sizeof(double) * (size_t)n_bkg * n_rec, cudaMemcpyHostToDevice, s), "upload bkg");
   }
   SRW_CUDA(h, launch_set_data(h, d_bkg, n_bkg, s), "data kernels");
@@ -894,6 +919,8 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
       if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
+    // a host-pointer call reports the device status of this call only
+    SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
     SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
              "theta upload");
     th = h->d_theta;
@@ -912,18 +939,41 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
       }
       return cudaSuccess;
     });
+  } else if (h->profile) {
+    // profiling: direct launches (no graph), with events around the fold
+    // kernel alone, so that srw_profile_read gives that kernel's device time
+    if (P == 1 && precision == SRW_FP32) {
+      cudaError_t e = launch_weights_from_basis(h, th, h->d_W, s);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_fold[0], s);
+      if (e == cudaSuccess) e = launch_fold_point(h, h->d_W, nullptr, nullptr, o, s, true);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_fold[1], s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "profiled single-point fold");
+    } else {
+      const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
+      st = ensure_bparts(h, (size_t)n_parts_max * P);
+      if (st == SRW_OK && precision == SRW_FP16X3) st = ensure_wscale(h, P);
+      if (st != SRW_OK) return st;
+      int n_parts = 0;
+      cudaError_t e = cudaSuccess;
+      if (precision == SRW_FP32) {
+        e = cudaEventRecord(h->ev_fold[0], s);
+        if (e == cudaSuccess) e = launch_fold_simt(h, th, P, h->d_bpart, s, &n_parts);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_fold[1], s);
+      } else {
+        e = launch_fold_tc(h, th, P, precision, h->cfg[precision], h->d_bpart, s, &n_parts, nullptr, h->ev_fold[0],
+                           h->ev_fold[1]);
+      }
+      if (e == cudaSuccess) e = launch_reduce_parts(h, h->d_bpart, n_parts, P, o, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "profiled batched fold");
+    }
   } else if (P == 1 && precision == SRW_FP32) {
     st = run_graph(h, 1, precision, P, th, o, s, [&](cudaStream_t cs) {
-      // W(theta) - W_ref from the coefficient spectra, then the HBM-streaming fold
+      // W(theta) - W_ref from the coefficient spectra, then the HBM-streaming
+      // fold, launched as a programmatic dependent: it streams R while the
+      // weights kernel runs
       cudaError_t e = launch_weights_from_basis(h, th, h->d_W, cs);
       if (e != cudaSuccess) return e;
-      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      // with profiling the fold runs after the recorded event; otherwise it
-      // overlaps its R stream with the weights kernel (programmatic dependency)
-      e = h->profile ? launch_fold_point(h, h->d_W, nullptr, nullptr, o, cs, true) : launch_fold_point_after(h, h->d_W, o, cs);
-      if (e != cudaSuccess) return e;
-      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      return cudaSuccess;
+      return launch_fold_point_after(h, h->d_W, o, cs);
     });
   } else {
     const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
@@ -933,12 +983,9 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
     const FoldConfig cfg = h->cfg[precision];
     st = run_graph(h, 2, precision, P, th, o, s, [&](cudaStream_t cs) {
       int n_parts = 0;
-      cudaError_t e;
-      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[0], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
-      e = precision == SRW_FP32 ? launch_fold_simt(h, th, P, h->d_bpart, cs, &n_parts)
-                                : launch_fold_tc(h, th, P, precision, cfg, h->d_bpart, cs, &n_parts);
+      cudaError_t e = precision == SRW_FP32 ? launch_fold_simt(h, th, P, h->d_bpart, cs, &n_parts)
+                                            : launch_fold_tc(h, th, P, precision, cfg, h->d_bpart, cs, &n_parts);
       if (e != cudaSuccess) return e;
-      if (h->profile && (e = cudaEventRecordWithFlags(h->ev_fold[1], cs, cudaEventRecordExternal)) != cudaSuccess) return e;
       return launch_reduce_parts(h, h->d_bpart, n_parts, P, o, cs);
     });
   }
@@ -979,12 +1026,14 @@ srw_status srw_loglik_linear(srw_handle h, const float* theta, int P, double* ou
       if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
+    // a host-pointer call reports the device status of this call only
+    SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
     SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
              "theta upload");
     th = h->d_theta;
     o = h->d_out;
     if (grad) {
-      SRW_CUDA(h, cudaMallocAsync(&d_g, sizeof(double) * 5 * (size_t)P, s), "alloc gradient");
+      SRW_CUDA(h, dev_malloc_async(&d_g, sizeof(double) * 5 * (size_t)P, s), "alloc gradient");
       g = d_g;
     }
   }
@@ -1025,12 +1074,14 @@ srw_status srw_loglik_profiled(srw_handle h, const float* theta, int P, double s
       if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
+    // a host-pointer call reports the device status of this call only
+    SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
     SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
              "theta upload");
     th = h->d_theta;
     o = h->d_out;
     if (alpha) {
-      SRW_CUDA(h, cudaMallocAsync(&d_a, sizeof(double) * (size_t)P, s), "alloc alpha");
+      SRW_CUDA(h, dev_malloc_async(&d_a, sizeof(double) * (size_t)P, s), "alloc alpha");
       a = d_a;
     }
   }
@@ -1076,10 +1127,12 @@ srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* ou
       if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
+    // a host-pointer call reports the device status of this call only
+    SRW_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), s), "status reset");
     SRW_CUDA(h, cudaMemcpyAsync(h->d_theta, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s),
              "theta upload");
     th = h->d_theta;
-    SRW_CUDA(h, cudaMallocAsync(&d_tmp, sizeof(float) * (size_t)P * h->n_rec, s), "alloc spectra");
+    SRW_CUDA(h, dev_malloc_async(&d_tmp, sizeof(float) * (size_t)P * h->n_rec, s), "alloc spectra");
     o = d_tmp;
   }
   int n_parts = 0;
@@ -1181,9 +1234,10 @@ srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char
   SRW_CUDA(h, cudaEventCreate(&e0), "event");
   SRW_CUDA(h, cudaEventCreate(&e1), "event");
   float best = 1e30f;
-  int best_i = 0;
+  int best_i = -1, n_timed = 0;
   for (int i = 0; i < tc_num_configs(); ++i) {
     const FoldConfig c = tc_config(i);
+    ++n_timed;
     int n_parts = 0;
     cudaError_t e = launch_fold_tc(h, h->d_theta, P, pr, c, h->d_bpart, s, &n_parts);  // warm-up
     if (e != cudaSuccess) continue;
@@ -1202,6 +1256,8 @@ srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (best_i < 0) return fail(h, SRW_ECUDA, "no fold configuration ran");
+  h->cfg_timed[pr] = n_timed;
   h->cfg[pr] = tc_config(best_i);
   h->cfg_index[pr] = best_i;
   destroy_graphs(h);
@@ -1210,6 +1266,44 @@ srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char
     std::ofstream o(cache_path, std::ios::app);
     o << key << " " << best_i << "\n";
   }
+  return SRW_OK;
+}
+
+srw_status srw_fold_config(int index, int* tile, int* k_block, int* stages) {
+  if (index < 0 || index >= tc_num_configs()) return SRW_EINVAL;
+  const FoldConfig c = tc_config(index);
+  if (tile) *tile = c.bn;
+  if (k_block) *k_block = c.bk;
+  if (stages) *stages = c.stages;
+  return SRW_OK;
+}
+
+srw_status srw_get_fold_config(srw_handle h, srw_precision precision, int* index, int* timed) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (precision == SRW_FP32 || precision < SRW_FP32 || precision > SRW_FP16X3)
+    return fail(h, SRW_EINVAL, "precision must be a tensor-core precision");
+  int idx = h->cfg_index[precision];
+  if (idx < 0)  // the default of the precision
+    for (int i = 0; i < tc_num_configs(); ++i) {
+      const FoldConfig c = tc_config(i);
+      if (c.bn == h->cfg[precision].bn && c.bk == h->cfg[precision].bk && c.stages == h->cfg[precision].stages) {
+        idx = i;
+        break;
+      }
+    }
+  if (index) *index = idx;
+  if (timed) *timed = h->cfg_timed[precision];
+  return SRW_OK;
+}
+
+srw_status srw_set_fold_config(srw_handle h, srw_precision precision, int index) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (precision == SRW_FP32 || precision < SRW_FP32 || precision > SRW_FP16X3)
+    return fail(h, SRW_EINVAL, "precision must be a tensor-core precision");
+  if (index < 0 || index >= tc_num_configs()) return fail(h, SRW_EINVAL, "no such fold configuration");
+  h->cfg[precision] = tc_config(index);
+  h->cfg_index[precision] = index;
+  destroy_graphs(h);
   return SRW_OK;
 }
 
@@ -1248,6 +1342,15 @@ srw_status srw_profile_read(srw_handle h, float* fold_ms) {
   if (!h->profile) return fail(h, SRW_EINVAL, "profiling is not enabled");
   SRW_CUDA(h, cudaEventSynchronize(h->ev_fold[1]), "event sync");
   SRW_CUDA(h, cudaEventElapsedTime(fold_ms, h->ev_fold[0], h->ev_fold[1]), "event elapsed");
+  return SRW_OK;
+}
+
+srw_status srw_check(srw_handle h, void* stream) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  bool domain = false;
+  srw_status st = check_status_word(h, pick_stream(h, stream), &domain);
+  if (st != SRW_OK) return st;
+  if (domain) return fail(h, SRW_EDOMAIN, "expected count <= 0 in a bin with data: a value is +inf");
   return SRW_OK;
 }
 

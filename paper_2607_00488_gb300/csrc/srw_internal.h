@@ -30,6 +30,29 @@ constexpr int kNB = 8;
 // Status bits written by kernels into the context's device status word.
 constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kStatusDomain = 2u;
+constexpr unsigned kStatusCheck = 4u;  // a debug-build bounds check failed
+
+// Debug-build bounds checks (compiled with -DSRW_DEBUG_CHECKS, the library
+// libsrw_debug.so): a failed check sets kStatusCheck in the kernel's status
+// word and the kernel carries on (no trap: the GPU and the context stay
+// usable); host-pointer calls and srw_check then report SRW_ECHECK.  In the
+// release build the checks compile to nothing.
+#ifdef SRW_DEBUG_CHECKS
+#define SRW_CHECK(status_ptr, cond)                                \
+  do {                                                             \
+    if (!(cond)) atomicOr((status_ptr), ::srw::kStatusCheck);      \
+  } while (0)
+constexpr bool kDebugChecks = true;
+#else
+#define SRW_CHECK(status_ptr, cond) \
+  do {                              \
+  } while (0)
+constexpr bool kDebugChecks = false;
+#endif
+// Canary doubles after the batched partial sums (debug build): a write past
+// the end of that buffer changes them, which host-pointer calls detect.
+constexpr int kCanaryDoubles = 64;
+constexpr unsigned long long kCanaryBits = 0x7ff4dead5ca1ab1eull;  // a signalling-NaN pattern
 
 // Device-side view of the theta-independent model tables.
 struct ModelView {
@@ -83,7 +106,7 @@ struct TcGroup {
   const CUtensorMap* map_hi;   // R hi / lo maps, box 64 K x bn rows (grouped launches; global memory)
   const CUtensorMap* map_lo;
   const float4* shat_k8;       // [k_pad][8] coefficient spectra, k-major
-  const float4* nb4;           // [n_rec] {n_j (0 where masked), b_j + R W_ref, mask 1/0, 1/r_j (FP16 row scale)}
+  const float4* nb4;           // [n_rec] {n_j (0 where masked), b_j + R W_ref - n_j, mask 1/0, 1/r_j (FP16 row scale)}
   const double* c_data;        // data constant of -2 ln L (device scalar)
   long long parts_off;         // partial sums of the group: parts + parts_off, [n_tiles][P]
   int n_rec, k_pad, P, p_off;  // p_off: first point of the group in the launch's theta / out
@@ -91,7 +114,7 @@ struct TcGroup {
   float sin2w_hi, sin2w_lo;
   CoefRef cref;
   const float* rinv;           // SRW_FP16X3: [n_rec] inverse power-of-two row scales of R
-  const int2* kbr;             // [n_tiles] K-block range {first, end} holding the tile's nonzero response
+  const int2* kbr;             // [n_tiles] K-block walk {first block, +-count} over the tile's nonzero response
   float wmax[kNB];             // SRW_FP16X3: max_i |shat_b,i| (bound of the weighted-spectrum deviations)
 };
 
@@ -107,7 +130,8 @@ struct GroupPart {
 struct FoldConfig {
   int kind;      // 0 = SIMT FP32, 1 = tcgen05
   int bn;        // rec-bin tile (N)
-  int stages;
+  int bk;        // true bins per pipeline stage (K block)
+  int stages;    // pipeline depth (shared-memory stages)
   int w_warps;   // producer warps for the weighted-spectrum operand
 };
 
@@ -165,7 +189,7 @@ struct srw_ctx {
   double* d_b64 = nullptr;
   float4* d_nbm = nullptr;
   float2* d_nb2 = nullptr;     // {n_j or -1 where masked, b_j + R W_ref} (surrogate epilogue)
-  float4* d_nb4 = nullptr;     // {n_j (0 where masked), b_j + R W_ref, mask 1/0, 1/r_j} (tensor-core epilogue)
+  float4* d_nb4 = nullptr;     // {n_j (0 where masked), b_j + R W_ref - n_j, mask 1/0, 1/r_j} (tensor-core epilogue)
   unsigned char* d_mask = nullptr;
   double* d_cdata = nullptr;
 
@@ -189,6 +213,7 @@ struct srw_ctx {
   std::vector<srw::GraphEntry> graphs;
   srw::FoldConfig cfg[4];      // per precision
   int cfg_index[4] = {-1, -1, -1, -1};
+  int cfg_timed[4] = {0, 0, 0, 0};  // candidates the last srw_autotune timed, per precision
   bool tensor_ok = false;
   void* tmap = nullptr;        // TMA descriptors for R hi/lo (tcgen05 path)
   int profile = 0;             // record events around the fold launch
@@ -203,6 +228,38 @@ struct srw_ctx {
 };
 
 namespace srw {
+
+// fault.cu: host-side fault injection (see srw_fault_inject in srw.h).
+// True when an armed fault of `kind` fires at this event (it then disarms).
+bool fault_fire(int kind);
+// True if a timeout fault fired on this thread since the last call (clears it).
+bool fault_take_timeout_fired();
+
+// Device allocation of the library (subject to SRW_FAULT_ALLOC injection).
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  if (fault_fire(SRW_FAULT_ALLOC)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+  if (fault_fire(SRW_FAULT_ALLOC)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+}
+// Status of the kernel launch just made (subject to SRW_FAULT_LAUNCH injection).
+inline cudaError_t launch_result() {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && fault_fire(SRW_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
+  return e;
+}
+// 1 when this fold launch is to take an injected timeout (SRW_FAULT_TIMEOUT).
+inline int inject_timeout() { return fault_fire(SRW_FAULT_TIMEOUT) ? 1 : 0; }
 
 srw_status fail(srw_ctx* h, srw_status s, const std::string& msg);
 srw_status cuda_fail(srw_ctx* h, cudaError_t e, const char* what);
@@ -256,7 +313,8 @@ void tc_release(srw_ctx* h);
 int tc_num_configs();
 FoldConfig tc_config(int i);
 cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int precision, const FoldConfig& cfg,
-                           double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr);
+                           double* parts, cudaStream_t s, int* n_parts, float* musig_out = nullptr,
+                           cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 cudaError_t launch_split_r(srw_ctx* h, cudaStream_t s);
 // linear.cu: exact rank-8 evaluation mu = mu_ref + b + M (c(theta) - c_ref).
 cudaError_t launch_linear_m(srw_ctx* h, cudaStream_t s);
@@ -278,8 +336,8 @@ cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s);
 // Fraction of the (rec tile, K block) pairs a batched fold executes.
 double tc_block_fraction(const srw_ctx* h, int bn, bool f16);
 // Tensor maps of h's hi / lo response (FP16 split if f16, else BF16) with a
-// box of 64 K x bn rows.
-cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo);
+// box of bk (64 or 32) K x bn rows.
+cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, CUtensorMap* lo, int bk = 64);
 // One persistent launch of n_cta CTAs over several configurations.  Slot
 // k * n_cta + b of items (n_slots in all) is CTA b's k-th item {group, m0,
 // n0, 0}; a group < 0 ends that CTA's list.  bn_max (128 or 256) bounds every

@@ -75,6 +75,34 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for rows of 64 bytes (32 BF16/FP16 along K): 64-byte swizzle,
+// 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                  // LBO (unused) = 16 B
+  d |= (uint64_t)(512u >> 4) << 32;         // SBO = 512 B
+  d |= (uint64_t)1u << 46;                  // descriptor version for sm_100 family
+  d |= (uint64_t)4u << 61;                  // 64-byte swizzle
+  return d;
+}
+
+// Descriptor of a K-major tile whose rows hold BK 16-bit elements (BK = 64 or 32).
+template <int BK>
+__device__ __forceinline__ uint64_t smem_desc_k(uint32_t saddr) {
+  static_assert(BK == 64 || BK == 32, "rows of 128 or 64 bytes");
+  return BK == 64 ? smem_desc_sw128(saddr) : smem_desc_sw64(saddr);
+}
+
+// Byte offset of 16-byte chunk `ch` of tile row `row` in the swizzled K-major
+// layout that TMA writes and the descriptors above read: rows of 2 BK bytes,
+// the chunk index XOR-ed with row bits (128-byte swizzle: row & 7; 64-byte
+// swizzle: (row >> 1) & 3).
+template <int BK>
+__device__ __forceinline__ uint32_t swz_offset(int row, int ch) {
+  return BK == 64 ? (uint32_t)(row * 128 + ((ch ^ (row & 7)) << 4))
+                  : (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4));
+}
+
 // Instruction descriptor, kind::f16, FP32 accumulator, both operands K-major
 // and of one type: BF16 x BF16 (operand format 1) or F16 x F16 (format 0).
 __host__ __device__ constexpr uint32_t idesc_f16kind(int m, int n, bool f16) {

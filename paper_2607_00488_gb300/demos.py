@@ -5,8 +5,8 @@ Asimov data are the expected counts at an injected point (no fluctuation), so
 at their injected values recovers it, and the points where -2 ln L rises by
 2.706 above its minimum bound the 90 % confidence interval for one parameter
 (Wilks' theorem; the paper's sensitivity study, Sec. VI, scans epsilon^L_ee and
-mu_nu this way).  The expected counts come from the library itself (the folded
-signal of srw_spectrum plus the background templates).
+mu_nu this way).  The expected counts come from the library itself
+(srw_spectrum stage 3: the folded signal plus the background templates).
 
     python -m paper_2607_00488_gb300.demos          # solar set: eps^L_ee and mu_nu
 """
@@ -23,10 +23,11 @@ from . import srw as _srw
 DCHI2_90 = 2.705543454095404  # chi^2 (1 dof) quantile at 0.90
 
 
-def asimov_counts(lk, wl, theta_inj):
-    """Expected counts at theta_inj: the library's folded signal plus the summed background."""
-    sig = lk.spectrum(np.asarray(theta_inj, np.float32), 2).astype(np.float64)
-    return sig + np.asarray(wl["bkg"], np.float64).reshape(-1, sig.size).sum(axis=0)
+def asimov_counts(lk, theta_inj):
+    """Expected counts at theta_inj (eq. mu_total): srw_spectrum stage 3 of the
+    library, the folded signal plus the summed background templates of the
+    handle's data set."""
+    return lk.spectrum(np.asarray(theta_inj, np.float32), 3).astype(np.float64)
 
 
 def interval(grid, values, level=DCHI2_90):
@@ -65,7 +66,13 @@ def asimov_study(wl, theta_inj, scans, evaluate="fp16x3", counts=None):
     `scans`.  Returns one interval() result per scan."""
     theta_inj = np.asarray(theta_inj, np.float64)
     with _srw.Likelihood(wl) as lk:
-        n = asimov_counts(lk, wl, theta_inj) if counts is None else np.asarray(counts, np.float64)
+        if counts is None:
+            # the background templates first (no counts yet), so that stage 3
+            # returns the expectation at the injected point
+            _srw.srw_set_data(lk.handle, np.zeros(wl["R"].shape[0]), wl.get("bkg"))
+            n = asimov_counts(lk, theta_inj)
+        else:
+            n = np.asarray(counts, np.float64)
         _srw.srw_set_data(lk.handle, n, wl.get("bkg"))
         lk.set_reference(theta_inj)  # fold deviations from the injected point
         out = []

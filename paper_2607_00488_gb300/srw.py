@@ -15,9 +15,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsrw.so")
+# SRW_LIB=debug selects the debug build (bounds checks compiled in, SRW_ECHECK)
+LIB_PATH = os.path.join(_HERE, "libsrw_debug.so" if os.environ.get("SRW_LIB") == "debug" else "libsrw.so")
 
-SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOUT, SRW_EUNSUPPORTED = range(8)
+SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOUT, SRW_EUNSUPPORTED, SRW_ECHECK = range(9)
 SRW_HOST, SRW_DEVICE = 0, 1
 SRW_FP32, SRW_BF16, SRW_BF16X3, SRW_FP16X3 = 0, 1, 2, 3
 SRW_SCAN_FLAG_CELLS, SRW_SCAN_ERROR_BARS = 0, 1
@@ -33,7 +34,9 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_surrogate_last_error", "srw_surrogate_destroy", "srw_surrogate_fit", "srw_surrogate_loglik",
            "srw_surrogate_scan", "srw_surrogate_scan_exact", "srw_surrogate_sobol", "srw_surrogate_get_standardization",
            "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled", "srw_create_joint", "srw_joint_layout",
-           "srw_fold_work")
+           "srw_fold_work", "srw_fault_inject", "srw_fault_pending", "srw_fault_parse", "srw_fold_config",
+           "srw_set_fold_config", "srw_check", "srw_get_fold_config",
+           "srw_surrogate_save", "srw_surrogate_load", "srw_surrogate_fit_resume", "srw_surrogate_scan_chunked")
 
 
 class SrwError(RuntimeError):
@@ -147,12 +150,26 @@ def lib():
         L.srw_surrogate_fit.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(_FitOpts), vp]
         L.srw_surrogate_loglik.argtypes = [vp, vp, ip, vp, ip, vp]
         L.srw_surrogate_scan.argtypes = [vp, ctypes.POINTER(_ScanOpts), ctypes.POINTER(_ScanResult)]
+        L.srw_surrogate_scan_chunked.argtypes = [vp, ctypes.POINTER(_ScanOpts), ctypes.c_longlong, ctypes.c_char_p, ip,
+                                                 ctypes.POINTER(_ScanResult), ctypes.POINTER(ctypes.c_int)]
+        L.srw_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        L.srw_surrogate_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong)]
+        L.srw_surrogate_fit_resume.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(_FitOpts), ip, ip,
+                                               ctypes.c_char_p, vp]
         L.srw_surrogate_scan_exact.argtypes = [vp, ctypes.c_longlong, ctypes.c_longlong, ip,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                                ctypes.POINTER(ctypes.c_float)]
         L.srw_surrogate_sobol.argtypes = [vp, ctypes.c_longlong, ip, vp]
         L.srw_surrogate_get_standardization.argtypes = [vp, vp, vp]
         L.srw_diag_wait_timeout.argtypes = [ctypes.c_uint]
+        L.srw_fault_inject.argtypes = [ip, ctypes.c_longlong]
+        L.srw_fold_config.argtypes = [ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
+        L.srw_set_fold_config.argtypes = [vp, ip, ip]
+        L.srw_get_fold_config.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.srw_check.argtypes = [vp, vp]
+        L.srw_fault_pending.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        L.srw_fault_parse.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
         L.srw_loglik_linear.argtypes = [vp, vp, ip, vp, vp, ip, vp]
         L.srw_loglik_profiled.argtypes = [vp, vp, ip, ctypes.c_double, vp, vp, ip, vp]
         L.srw_surrogate_last_error.argtypes = [vp]
@@ -399,6 +416,36 @@ def srw_autotune(h, P, precision, cache_path=None, stream=None):
     return chosen.value
 
 
+def srw_fold_config(index):
+    """(tile, k_block, stages) of tensor-core fold configuration `index`; None past the last."""
+    t, k, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    if lib().srw_fold_config(int(index), ctypes.byref(t), ctypes.byref(k), ctypes.byref(st)) != SRW_OK:
+        return None
+    return t.value, k.value, st.value
+
+
+def srw_fold_configs():
+    """All tensor-core fold configurations as (index, tile, k_block, stages)."""
+    out, i = [], 0
+    while True:
+        c = srw_fold_config(i)
+        if c is None:
+            return out
+        out.append((i,) + c)
+        i += 1
+
+
+def srw_get_fold_config(h, precision):
+    """(configuration index in use, candidates timed by the last autotune)."""
+    i, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().srw_get_fold_config(h, int(precision), ctypes.byref(i), ctypes.byref(t)), h)
+    return i.value, t.value
+
+
+def srw_set_fold_config(h, precision, index):
+    _check(lib().srw_set_fold_config(h, int(precision), int(index)), h)
+
+
 def srw_fold_work(h, precision, tile=0):
     """Fraction of the (rec tile, K block) pairs the batched fold executes
     (tile 0: the handle's configured rec-tile width)."""
@@ -435,10 +482,76 @@ def srw_profile_read(h):
     return ms.value
 
 
+def _check_noalloc_args(R, W, counts, out, bkg, mask):
+    """Host-side checks of srw_loglik_point_noalloc's tensors (no device work)."""
+    named = [("R", R, "float32"), ("W", W, "float32"), ("counts", counts, "float64"), ("out", out, "float64")]
+    if bkg is not None:
+        named.append(("bkg", bkg, "float64"))
+    if mask is not None:
+        named.append(("mask", mask, "uint8"))
+    devices = set()
+    for name, t, dtype in named:
+        if not (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False)):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if str(t.dtype) != "torch." + dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, str(t.dtype).replace("torch.", "")))
+        devices.add(t.device)
+    if len(devices) != 1:
+        raise ValueError("all tensors must be on one device")
+    if R.dim() != 2:
+        raise ValueError("R must be 2-D (n_rec, ld)")
+    n_rec, ld = R.shape
+    if W.numel() < ld:
+        raise ValueError("W holds %d values, R's rows %d" % (W.numel(), ld))
+    for name, t in (("counts", counts), ("bkg", bkg), ("mask", mask)):
+        if t is not None and t.numel() != n_rec:
+            raise ValueError("%s must hold n_rec = %d values, got %d" % (name, n_rec, t.numel()))
+    if out.numel() < 1:
+        raise ValueError("out must hold at least one value")
+
+
+SRW_FAULT_NONE, SRW_FAULT_ALLOC, SRW_FAULT_LAUNCH, SRW_FAULT_TIMEOUT = 0, 1, 2, 3
+FAULT_KINDS = {"none": SRW_FAULT_NONE, "alloc": SRW_FAULT_ALLOC, "launch": SRW_FAULT_LAUNCH,
+               "timeout": SRW_FAULT_TIMEOUT}
+
+
+def srw_fault_inject(kind, skip=0):
+    """Arm a one-shot host-side fault ("alloc", "launch", "timeout" or "none"):
+    it fires at the (skip+1)-th matching event and then disarms."""
+    k = FAULT_KINDS[kind] if isinstance(kind, str) else int(kind)
+    st = lib().srw_fault_inject(k, int(skip))
+    if st != SRW_OK:
+        raise SrwError(st, "bad fault kind or skip")
+
+
+def srw_fault_pending():
+    """The armed fault kind (0 when none is armed)."""
+    k = ctypes.c_int()
+    lib().srw_fault_pending(ctypes.byref(k))
+    return k.value
+
+
+def srw_fault_parse(spec):
+    """(kind, skip) of an SRW_FAULT specification; SrwError if it is not one."""
+    k, n = ctypes.c_int(), ctypes.c_longlong()
+    st = lib().srw_fault_parse(spec.encode(), ctypes.byref(k), ctypes.byref(n))
+    if st != SRW_OK:
+        raise SrwError(st, "not a fault specification: %r" % spec)
+    return k.value, n.value
+
+
 def srw_loglik_point_noalloc(R, W, counts, out, bkg=None, mask=None, stream=None):
     """Allocation-free single-point -2 ln L: every argument a CUDA tensor.
     R: (n_rec, ld) float32 with ld a multiple of 64; W: (ld,) float32;
-    counts, bkg: (n_rec,) float64; mask: (n_rec,) uint8 or None; out: (1,) float64."""
+    counts, bkg: (n_rec,) float64; mask: (n_rec,) uint8 or None; out: (1,) float64.
+
+    The library reads every size from n_rec and ld, so each tensor is checked
+    here first (ValueError): CUDA, contiguous, one device, the dtypes above,
+    and long enough for the reads the kernels make.  A timed-out device wait
+    leaves NaN in out[0] (the call itself is asynchronous and returns first)."""
+    _check_noalloc_args(R, W, counts, out, bkg, mask)
     n_rec, ld = R.shape
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     st = lib().srw_loglik_point_noalloc(ptr(R), int(n_rec), int(ld), ptr(W), ptr(counts), ptr(bkg), ptr(mask),
@@ -589,6 +702,11 @@ def srw_surrogate_destroy(sg):
         lib().srw_surrogate_destroy(sg)
 
 
+def srw_check(h, stream=None):
+    """Device-side status of the handle's device-pointer calls (raises SrwError)."""
+    _check(lib().srw_check(h, _stream(stream) if stream is not None else None), h)
+
+
 def srw_last_error(h):
     return lib().srw_last_error(h).decode(errors="replace")
 
@@ -634,6 +752,14 @@ class Likelihood:
 
     def loglik_points(self, theta, out=None, stream=None):
         return srw_loglik_points(self.handle, theta, out, stream)
+
+    def check(self, stream=None):
+        """Raise SrwError if a device-pointer call since the last check timed out
+        (its affected values are NaN) or produced +inf."""
+        srw_check(self.handle, stream)
+
+    def set_fold_config(self, precision, index):
+        srw_set_fold_config(self.handle, precision, index)
 
     def set_reference(self, theta_ref):
         srw_set_reference(self.handle, theta_ref)
@@ -750,6 +876,48 @@ class Surrogate:
         _scheck(lib().srw_surrogate_fit(self.handle, th.ctypes.data, th.shape[0], ctypes.byref(o), losses.ctypes.data),
                 self.handle)
         return losses[:int(epochs)]
+
+    def save(self, path):
+        """Checkpoint the whole training state (srw_surrogate_save)."""
+        _scheck(lib().srw_surrogate_save(self.handle, os.fsencode(path)), self.handle)
+
+    def load(self, path):
+        """Restore a checkpoint; returns the completed epochs it records."""
+        done = ctypes.c_longlong()
+        _scheck(lib().srw_surrogate_load(self.handle, os.fsencode(path), ctypes.byref(done)), self.handle)
+        return done.value
+
+    def fit_resumable(self, theta, epochs, checkpoint, batch=8192, lr=1e-3, lr_final=1e-5, precision=None,
+                      stop_after=None):
+        """The fit of fit() with a checkpoint after every epoch: if `checkpoint`
+        exists it is loaded and the fit continues after its last completed
+        epoch.  stop_after (epochs of this call) ends the call early, as an
+        interruption would.  Returns the losses of the epochs this call ran."""
+        th = _f32(theta).reshape(-1, 5)
+        first = self.load(checkpoint) if os.path.exists(checkpoint) else 0
+        stop = int(epochs) if stop_after is None else min(int(epochs), first + int(stop_after))
+        o = _FitOpts(int(batch), int(epochs), float(lr), float(lr_final),
+                     int(SRW_FP16X3 if precision is None else precision))
+        losses = np.zeros(max(1, int(epochs)), dtype=np.float32)
+        if stop > first:
+            _scheck(lib().srw_surrogate_fit_resume(self.handle, th.ctypes.data, th.shape[0], ctypes.byref(o), first,
+                                                   stop, os.fsencode(checkpoint), losses.ctypes.data), self.handle)
+        return losses[first:stop]
+
+    def scan_chunked(self, n_points, state_path, chunk_points, first=0, keep_frac=0.01, check_theta=None, tol=0.05,
+                     cells_per_dim=4, precision=None, rule=SRW_SCAN_FLAG_CELLS, margin_factor=2.0, max_new_chunks=0):
+        """srw_surrogate_scan_chunked: returns (result dict, complete)."""
+        chk = None if check_theta is None else _f32(check_theta).reshape(-1, 5)
+        o = _ScanOpts(int(first), int(n_points), float(keep_frac), chk.ctypes.data if chk is not None else None,
+                      0 if chk is None else chk.shape[0], float(tol), int(cells_per_dim),
+                      int(SRW_FP16X3 if precision is None else precision), int(rule), float(margin_factor))
+        r = _ScanResult()
+        done = ctypes.c_int()
+        _scheck(lib().srw_surrogate_scan_chunked(self.handle, ctypes.byref(o), int(chunk_points),
+                                                 os.fsencode(state_path), int(max_new_chunks), ctypes.byref(r),
+                                                 ctypes.byref(done)), self.handle)
+        res = {name: (list(getattr(r, name)) if name == "best_theta" else getattr(r, name)) for name, _ in r._fields_}
+        return res, bool(done.value)
 
     def loglik(self, theta, out=None, stream=None):
         """Surrogate -2 ln L (host theta -> numpy; CUDA tensors -> written into out)."""

@@ -135,3 +135,15 @@ def test_valid_create_without_a_device_fails_loudly(srw):
     with pytest.raises(srw.SrwError) as ei:
         srw.srw_create(a["t_edges"], a["n_rec"], a["sources"], a["R"], a["exposure"])
     assert ei.value.status in (3, 7)  # SRW_ECUDA, SRW_EUNSUPPORTED
+
+
+def test_debug_build_exports_every_declared_symbol():
+    """libsrw_debug.so (bounds checks compiled in) builds and exports the same
+    boundary as the release library."""
+    import ctypes
+    from paper_2607_00488_gb300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libsrw_debug.so")
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name

@@ -162,6 +162,21 @@ def _budget(m, th, mu_sig_gpu):
     return 2.0 * np.sum(np.abs(1.0 - m.counts[on] / mu[on]) * np.abs(dmu[on]))
 
 
+def _eval_budget(m, th, prec):
+    """Bound of the tensor-core epilogue's own FP32 evaluation of the deviance
+    terms t_j = n_j ln(n_j/mu_j) + (mu_j - n_j): about three roundings of
+    2^-24 on each of the two parts, doubled in -2 ln L = C + 2 sum_j t_j.  Far
+    from the data the parts are large and cancel only partly, so this can
+    exceed the fold's budget B; the FP32 SIMT fold evaluates them in FP64."""
+    if prec == 0:
+        return 0.0
+    mu = m.oracle().mu(th.astype(np.float64))
+    n = m.counts
+    on = mu > 0
+    nlog = np.where(n[on] > 0, n[on] * np.abs(np.log(np.where(n[on] > 0, n[on], 1.0) / mu[on])), 0.0)
+    return 2.0 * 3.0 * 2.0 ** -24 * float(np.sum(nlog + np.abs(mu[on] - n[on])))
+
+
 def _check_vs_oracle(srw, members, got_by_member, prec, idx_fn):
     worst = []
     for m, g in zip(members, got_by_member):
@@ -174,8 +189,9 @@ def _check_vs_oracle(srw, members, got_by_member, prec, idx_fn):
             musig = m.lk.spectrum_batch(th[None, :], prec)[0]
             b = _budget(m, th, musig)
             fit = i < m.n_fit
+            e = _eval_budget(m, th, prec)
             worst.append((d, b, fit, m.wl["exposure"], m.wl["name"], i))
-            assert d <= TOL[prec] + 2.0 * b, (m.wl["name"], i, d, b)
+            assert d <= TOL[prec] + 2.0 * b + e, (m.wl["name"], i, d, b, e)
             if fit and (prec == 0 or m.wl["exposure"] <= 1e5):
                 assert d <= TOL[prec], (m.wl["name"], i, d, b)
     return worst

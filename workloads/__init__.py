@@ -23,6 +23,8 @@ from .solar import (  # noqa: F401
     group_counts_path,
     load_group_counts,
     theta_box,
+    fit_region_points,
+    box_sample,
     poisson_counts,
     load_counts,
     counts_path,

@@ -188,6 +188,23 @@ def theta_box(p, seed, eps_max=0.3, mu_max=3.0):
     return np.ascontiguousarray(th, dtype=np.float32)
 
 
+def fit_region_points(n, seed=99, eps_max=0.02, mu_max=0.5):
+    """Points near the SM (|eps| <= eps_max, mu_hat <= mu_max): where a fit or a
+    confidence interval on 1e5-event data is decided.  Seed 99, n = 8 are the
+    benchmark's parity points."""
+    rng = np.random.default_rng(seed)
+    th = np.zeros((n, 5), np.float32)
+    th[:, :4] = rng.uniform(-eps_max, eps_max, (n, 4))
+    th[:, 4] = rng.uniform(0.0, mu_max, n)
+    return th
+
+
+def box_sample(p, n, seed):
+    """n evenly spaced points of the P-point box batch theta_box(P, seed) (the
+    benchmark's box parity sample: P = 65536, n = 12, seed 3)."""
+    return theta_box(p, seed)[np.linspace(0, p - 1, n).astype(int)]
+
+
 def theta_grid_be7():
     g = np.linspace(-0.5, 0.5, 4)
     th = np.zeros((16, 5), dtype=np.float32)
