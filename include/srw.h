@@ -289,6 +289,15 @@ srw_status srw_get_fold_config(srw_handle h, srw_precision precision, int* index
  * result.  1 for SRW_FP32 (the SIMT fold runs every block). */
 srw_status srw_fold_work(srw_handle h, srw_precision precision, int tile, double* executed_fraction);
 
+/* Bytes of R the single-point fold (the GEMV of srw_loglik with P = 1 and
+ * SRW_FP32, and srw_spectrum stages 2-3) streams per call: each row's nonzero
+ * band [first nonzero column rounded down to 4 floats, a length rounded up to
+ * 32 floats), found at srw_create; outside it every element of R is an exact
+ * zero, so the GEMV skips it without changing its result (eq. visible_spectrum).
+ * The rows are split over the GEMV's blocks so that each streams about the
+ * same number of bytes. */
+srw_status srw_gemv_work(srw_handle h, long long* bytes);
+
 /* Sizes of a context. */
 typedef struct {
   int n_t, n_rec, n_nodes, k_pad;
@@ -545,7 +554,10 @@ srw_status srw_surrogate_scan_chunked(srw_surrogate s, const srw_scan_opts* opts
                                       int* complete);
 
 /* The same scan without the surrogate: the exact path on every point; the
- * minimum, its index and the device time. */
+ * minimum, its index and the device time.  `precision`: an srw_precision of
+ * the batched fold, or SRW_RANK8 for the exact rank-8 evaluator
+ * (srw_loglik_linear). */
+#define SRW_RANK8 16
 srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long n_points, int precision,
                                     double* best_value, long long* best_index, float* ms);
 

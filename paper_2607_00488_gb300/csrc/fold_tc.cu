@@ -177,13 +177,13 @@ __device__ __forceinline__ int kb_at(int2 kr, int kk) {
 }
 
 constexpr int kMaxGroups = 4096;  // configurations of one grouped launch
-constexpr int kKbrStaged = 64;    // rec tiles whose K-block walks a single-configuration CTA keeps in shared memory
 
-// K-block walk of the rec tile at n0 (shared-memory copy when staged).
+// K-block walk of the rec tile at n0.  (Staging the walks, or the epilogue's
+// per-bin constants, in shared memory was measured: no gain, and 4.8 % slower
+// for the constants.)
 template <bool GROUPED, int BN>
-__device__ __forceinline__ int2 tile_walk(const TcGroup& G, int n0, const int2* kbr_s) {
-  const int nt = n0 / (GROUPED ? G.bn : BN);
-  return (!GROUPED && nt < kKbrStaged) ? kbr_s[nt] : G.kbr[nt];
+__device__ __forceinline__ int2 tile_walk(const TcGroup& G, int n0) {
+  return G.kbr[n0 / (GROUPED ? G.bn : BN)];
 }
 
 // Kernel parameters.  A single-configuration launch walks the m x n tiles of
@@ -255,17 +255,9 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsmem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t r_full[ST], w_full[ST], empty[ST], acc_full[NB], acc_empty[NB], drain;
   __shared__ __align__(8) uint64_t s_full[kShatSlots], s_empty[kShatSlots], never;
-  // per-bin constants of the epilogue for the current and the next item,
-  // copied ahead by the TMA warp: {n_j, b_j + R W_ref - n_j, mask, 1/r_j}
-  __shared__ __align__(16) float4 nb_s[2][BN];
-  __shared__ __align__(8) uint64_t nb_full[2], nb_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ unsigned abort_flag;
   __shared__ uint32_t map_fenced[GROUPED ? kMaxGroups / 32 : 1];  // maps already acquired by the R producer
-  // K-block walks of a single configuration's rec tiles, staged once per CTA
-  // (every role reads one at each item start; from global memory that is a
-  // load latency on the pipeline's path per item)
-  __shared__ int2 kbr_s[GROUPED ? 1 : kKbrStaged];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned* status = L.status;
@@ -282,8 +274,6 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
 
   if (GROUPED)
     for (int i = threadIdx.x; i < kMaxGroups / 32; i += blockDim.x) map_fenced[i] = 0u;
-  if (!GROUPED)
-    for (int i = threadIdx.x; i < L.g0.n_tiles && i < kKbrStaged; i += blockDim.x) kbr_s[i] = L.g0.kbr[i];
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       ptx::mbar_init(&r_full[s], 1);
@@ -300,10 +290,6 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     }
     ptx::mbar_init(&drain, 1);
     ptx::mbar_init(&never, 1);  // nothing arrives on it (injected timeout)
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(&nb_full[b], 1);
-      ptx::mbar_init(&nb_empty[b], 4);
-    }
     abort_flag = 0u;
     ptx::fence_barrier_init();
   }
@@ -336,7 +322,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const float* theta = L.theta + (size_t)G.p_off * 5;
       const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
       // K blocks of this rec tile that hold nonzero response (the rest add exact zeros)
-      const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+      const int2 kr = tile_walk<GROUPED, BN>(G, n0);
       float c[4][kNB];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
@@ -427,13 +413,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const int bn = GROUPED ? G.bn : BN, nt = n0 / bn, n_rec = G.n_rec, P = G.P;
       const int buf = tc % NB;
       const int p = m0 + q * 32 + lane;
-      const int tb = tc & 1;  // constants buffer of this item
       if (!dead && __any_sync(0xffffffffu, aborted(&abort_flag))) dead = true;
       if (!dead && !warp_wait(&acc_full[buf], (tc / NB) & 1, &abort_flag, 256)) {
-        give_up();
-        dead = true;
-      }
-      if (!dead && parts != nullptr && !warp_wait(&nb_full[tb], (tc >> 1) & 1, &abort_flag)) {
         give_up();
         dead = true;
       }
@@ -459,7 +440,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           for (int k = 0; k < 16; ++k) {
             const int j = n0 + c0 + k;
             // {n_j (0 where masked), b_j + R W_ref - n_j, mask, 1/r_j}; padding columns add nothing
-            dj[k] = j < n_rec ? nb_s[tb][c0 + k] : make_float4(0.f, 1.f, 0.f, 0.f);
+            dj[k] = j < n_rec ? __ldg(G.nb4 + j) : make_float4(0.f, 1.f, 0.f, 0.f);
           }
         } else {  // folded spectra only (no data needed): just the row scales
 #pragma unroll
@@ -492,10 +473,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       if (mneg < 0.f) infinite = true;
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        ptx::mbar_arrive(&acc_empty[buf]);
-        if (parts != nullptr) ptx::mbar_arrive(&nb_empty[tb]);
-      }
+      if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
       if (parts != nullptr && p < P)
         parts[G.parts_off + (long long)nt * P + p] =
             infinite ? __longlong_as_double(0x7ff0000000000000LL) : (double)acc.hi + (double)acc.lo;
@@ -510,7 +488,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0);
         const uint32_t bytes = (uint32_t)((X3 ? 2 : 1) * (GROUPED ? G.bn : BN) * BK * 2);
         const CUtensorMap* mh = &map_hi;
         const CUtensorMap* ml = &map_lo;
@@ -549,7 +527,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0);
         for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
           const int kb = kb_at<BK>(kr, kk);
           const int sl = g % kShatSlots;
@@ -566,26 +544,6 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       }
       for (int u = max(0, issued - kShatSlots); u < issued; ++u)
         ptx::mbar_wait(&s_full[u % kShatSlots], (u / kShatSlots) & 1, nullptr, 100000000ull);
-    } else if (lane == 2 && parts != nullptr) {  // the epilogue's per-bin constants, one item ahead
-      int tc = -1, issued = 0;
-      FOR_ITEMS(idx) {
-        ++tc;
-        int m0, n0, gi;
-        const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
-        if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int tb = tc & 1;
-        if (!ptx::mbar_wait(&nb_empty[tb], ((tc >> 1) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
-          give_up();
-          break;
-        }
-        const int cnt = min(GROUPED ? G.bn : BN, G.n_rec - n0);  // >= 1: tiles start below n_rec
-        SRW_CHECK(status, cnt >= 1 && n0 >= 0);
-        ptx::mbar_arrive_expect_tx(&nb_full[tb], (uint32_t)cnt * 16u);
-        ptx::bulk_g2s(&nb_s[tb][0], G.nb4 + n0, (uint32_t)cnt * 16u, &nb_full[tb]);
-        issued = tc + 1;
-      }
-      for (int u = max(0, issued - 2); u < issued; ++u)  // never end with copies in flight
-        ptx::mbar_wait(&nb_full[u & 1], (u >> 1) & 1, nullptr, 100000000ull);
     }
   } else {
     // ------------------------------------------------------------ MMA issuer
@@ -599,7 +557,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         int m0, n0, gi;
         const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
         if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-        const int2 kr = tile_walk<GROUPED, BN>(G, n0, kbr_s);
+        const int2 kr = tile_walk<GROUPED, BN>(G, n0);
         const uint32_t idesc = idesc_f16kind(kBM, GROUPED ? G.bn : BN, F16);
         const int buf = tc % NB;
         if (!ptx::mbar_wait(&acc_empty[buf], ((tc / NB) & 1) ^ 1, &abort_flag)) {
@@ -928,15 +886,13 @@ static bool descending_is_better(const std::vector<float>& R, int ld, int n_rec,
 // blocks without changing a bit of the accumulation.  A tile without any
 // nonzero element keeps one block (its accumulator must still be written).
 // The device copy holds the walk {first block, +-count} (see kb_at).
-cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s) {
+cudaError_t tc_block_ranges(srw_ctx* h, const std::vector<float>& R, cudaStream_t s) {
   const int n_kb = h->k_pad / kBK;
   unsigned char* d_flags = nullptr;
   const int max_tiles = (h->n_rec + 127) / 128;
   cudaError_t e = dev_malloc(&d_flags, (size_t)max_tiles * n_kb);
   if (e != cudaSuccess) return e;
   std::vector<unsigned char> flags((size_t)max_tiles * n_kb);
-  std::vector<float> R((size_t)h->n_rec * h->ld_r);
-  e = cudaMemcpyAsync(R.data(), h->d_R, sizeof(float) * R.size(), cudaMemcpyDeviceToHost, s);
   // direction per group of 256 rows (both tile widths use it, so that every
   // output element accumulates the same updates in the same order whichever
   // width a launch uses; skipped blocks only ever add exact zeros)

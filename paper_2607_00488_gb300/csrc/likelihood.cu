@@ -12,7 +12,9 @@
 // Poisson term and the bin reduction are FP64 and fused into the same launch
 // (the last block to finish sums the per-block partials in block order).
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 #include <string>
 
 #include "dfloat.cuh"
@@ -48,7 +50,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
                   const unsigned char* __restrict__ mask, const double* __restrict__ c_data,
                   float* __restrict__ musig_out, float* __restrict__ mu_out, double* __restrict__ parts,
                   unsigned* __restrict__ ticket, double* __restrict__ out, unsigned* __restrict__ status,
-                  int inject) {
+                  int inject, const int2* __restrict__ band, const int* __restrict__ row_start) {
   extern __shared__ __align__(128) unsigned char dsmem[];
   const int chunk = ld < kGvChunk ? ld : kGvChunk;
   float* sbuf = reinterpret_cast<float*>(dsmem);
@@ -59,11 +61,15 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   __shared__ bool is_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = blockIdx.x * rows_per_block;
-  const int r1 = min(n_rec, r0 + rows_per_block);
+  // rows of this block: an even split, or (row_start) a split that balances
+  // the bytes of the rows' nonzero bands
+  const int r0 = row_start ? row_start[blockIdx.x] : blockIdx.x * rows_per_block;
+  const int r1 = row_start ? row_start[blockIdx.x + 1] : min(n_rec, r0 + rows_per_block);
   const int nrows = r1 > r0 ? r1 - r0 : 0;
-  const int cpr = (ld + chunk - 1) / chunk;  // chunks per row
-  const int n_units = nrows * cpr;
+  // columns of row r that are streamed: its nonzero band (a multiple of 32
+  // floats, 16-byte aligned), else the whole padded row; outside the band
+  // every element of R is an exact zero, so skipping it changes nothing
+  auto row_band = [&](int r) { return band ? band[r] : make_int2(0, ld); };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kGvStages; ++st) {
@@ -79,20 +85,24 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   if (warp == kGvConsumers) {
     // ---- producer (one lane)
     if (lane == 0) {
-      int issued = 0;
-      for (int u = 0; u < n_units; ++u) {
-        const int st = u % kGvStages;
-        if (u >= kGvStages && !ptx::mbar_wait(&empty[st], ((u / kGvStages) - 1) & 1, &abort_flag)) {
-          atomicExch(&abort_flag, 1u);
-          atomicOr(status, kStatusTimeout);
-          break;
+      int issued = 0, u = 0;
+      bool ok = true;
+      for (int row = r0; row < r1 && ok; ++row) {
+        const int2 b = row_band(row);
+        for (int k0 = b.x; k0 < b.y; k0 += chunk, ++u) {
+          const int st = u % kGvStages;
+          if (u >= kGvStages && !ptx::mbar_wait(&empty[st], ((u / kGvStages) - 1) & 1, &abort_flag)) {
+            atomicExch(&abort_flag, 1u);
+            atomicOr(status, kStatusTimeout);
+            ok = false;
+            break;
+          }
+          const int len = min(chunk, b.y - k0);
+          SRW_CHECK(status, row < n_rec && k0 >= 0 && len > 0 && k0 + len <= ld && (len & 31) == 0);
+          ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)len * 4u);
+          ptx::bulk_g2s(sbuf + (size_t)st * chunk, R + (size_t)row * ld + k0, (uint32_t)len * 4u, &full[st]);
+          issued = u + 1;
         }
-        const int row = r0 + u / cpr, k0 = (u % cpr) * chunk;
-        const int len = min(chunk, ld - k0);
-        SRW_CHECK(status, row < n_rec && k0 >= 0 && len > 0 && k0 + len <= ld && (len & 3) == 0);
-        ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)len * 4u);
-        ptx::bulk_g2s(sbuf + (size_t)st * chunk, R + (size_t)row * ld + k0, (uint32_t)len * 4u, &full[st]);
-        issued = u + 1;
       }
       // never let the block end with copies in flight
       for (int u = max(0, issued - kGvStages); u < issued; ++u)
@@ -112,37 +122,41 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
       atomicOr(status, kStatusTimeout);
     }
     dfloat lacc = {0.f, 0.f};
-    for (int u = 0; u < n_units; ++u) {
-      const int st = u % kGvStages;
-      if (!ptx::mbar_wait(&full[st], (u / kGvStages) & 1, &abort_flag)) {
-        if (lane == 0) {
-          atomicExch(&abort_flag, 1u);
-          atomicOr(status, kStatusTimeout);
+    int u = 0;
+    bool ok = true;
+    for (int row = r0; row < r1 && ok; ++row) {
+      const int2 b = row_band(row);
+      for (int k0 = b.x; k0 < b.y; k0 += chunk, ++u) {
+        const int st = u % kGvStages;
+        if (!ptx::mbar_wait(&full[st], (u / kGvStages) & 1, &abort_flag)) {
+          if (lane == 0) {
+            atomicExch(&abort_flag, 1u);
+            atomicOr(status, kStatusTimeout);
+          }
+          ok = false;
+          break;
         }
-        break;
+        const int len = min(chunk, b.y - k0), slice = len / kGvConsumers;  // a multiple of 4 floats
+        const float4* buf = reinterpret_cast<const float4*>(sbuf + (size_t)st * chunk + warp * slice);
+        const float4* w4 = reinterpret_cast<const float4*>(W + k0 + warp * slice);
+        float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+        for (int q = lane; q < slice / 4; q += 32) {
+          const float4 r = buf[q];
+          const float4 w = __ldg(w4 + q);
+          ax = fmaf(r.x, w.x, ax);
+          ay = fmaf(r.y, w.y, ay);
+          az = fmaf(r.z, w.z, az);
+          aw = fmaf(r.w, w.w, aw);
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&empty[st]);
+        lacc = df_add(lacc, (ax + ay) + (az + aw));
       }
-      const int c = u % cpr, k0 = c * chunk;
-      const int len = min(chunk, ld - k0), slice = len / kGvConsumers;  // a multiple of 8 floats
-      const float4* buf = reinterpret_cast<const float4*>(sbuf + (size_t)st * chunk + warp * slice);
-      const float4* w4 = reinterpret_cast<const float4*>(W + k0 + warp * slice);
-      float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
-      for (int q = lane; q < slice / 4; q += 32) {
-        const float4 r = buf[q];
-        const float4 w = __ldg(w4 + q);
-        ax = fmaf(r.x, w.x, ax);
-        ay = fmaf(r.y, w.y, ay);
-        az = fmaf(r.z, w.z, az);
-        aw = fmaf(r.w, w.w, aw);
-      }
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&empty[st]);
-      lacc = df_add(lacc, (ax + ay) + (az + aw));
-      if (c == cpr - 1) {
-        SRW_CHECK(status, u / cpr < rows_per_block);
-        const dfloat v = df_warp_sum(lacc);
-        if (lane == 0) spart[(u / cpr) * kGvConsumers + warp] = make_float2(v.hi, v.lo);
-        lacc = {0.f, 0.f};
-      }
+      if (!ok) break;
+      SRW_CHECK(status, row - r0 < rows_per_block);
+      const dfloat v = df_warp_sum(lacc);  // the row's sum (every row has at least one chunk)
+      if (lane == 0) spart[(row - r0) * kGvConsumers + warp] = make_float2(v.hi, v.lo);
+      lacc = {0.f, 0.f};
     }
   }
   __syncthreads();
@@ -266,19 +280,71 @@ __global__ void cdata_kernel(const double* __restrict__ n64, const unsigned char
 
 }  // namespace
 
-static int gv_rows_per_block(const srw_ctx* h) {
+static int gv_uniform_rows(const srw_ctx* h) {
   const int g = h->sm_count > 0 ? h->sm_count : 148;
   return (h->n_rec + g - 1) / g;
 }
 
+// Rows per block: the even split, or the largest block of the band-balanced split.
+static int gv_rows_per_block(const srw_ctx* h) { return h->gv_blocks > 0 ? h->gv_max_rows : gv_uniform_rows(h); }
+
 int fold_point_grid(const srw_ctx* h) {
-  const int rpb = gv_rows_per_block(h);
+  const int rpb = gv_uniform_rows(h);
   return (h->n_rec + rpb - 1) / rpb;
 }
 
 static size_t gv_smem(const srw_ctx* h) {
   const int chunk = h->ld_r < kGvChunk ? h->ld_r : kGvChunk;
   return sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * (size_t)kGvConsumers * gv_rows_per_block(h);
+}
+
+// Per row of R its nonzero band [lo, hi): lo the first nonzero column rounded
+// down to 4 floats (16-byte copies), the length rounded up to 32 floats (eight
+// consumer warps x float4) and kept inside the padded row; an all-zero row
+// keeps 32 columns.  Then the rows are split over the fold_point_grid blocks
+// so that each streams about the same number of bytes (plus a per-row cost).
+cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R) {
+  const int n_rec = h->n_rec, ld = h->ld_r;
+  std::vector<int2> band(n_rec);
+  long long total = 0;
+  for (int r = 0; r < n_rec; ++r) {
+    const float* row = R.data() + (size_t)r * ld;
+    int first = -1, last = -1;
+    for (int k = 0; k < ld; ++k)
+      if (row[k] != 0.f) {
+        if (first < 0) first = k;
+        last = k;
+      }
+    int lo = first < 0 ? 0 : first / 4 * 4;
+    int len = first < 0 ? 32 : (last + 1 - lo + 31) / 32 * 32;
+    if (len > ld) len = ld;
+    if (lo + len > ld) lo = ld - len;
+    band[r] = make_int2(lo, lo + len);
+    total += len + 64;  // + a per-row cost (the row's reduction and epilogue)
+  }
+  const int nb = fold_point_grid(h);
+  std::vector<int> start(nb + 1, n_rec);
+  start[0] = 0;
+  long long acc = 0;
+  int b = 1, max_rows = 0;
+  for (int r = 0; r < n_rec && b < nb; ++r) {
+    acc += band[r].y - band[r].x + 64;
+    if (acc * nb >= total * b) start[b++] = r + 1;
+  }
+  for (int k = 0; k < nb; ++k) max_rows = std::max(max_rows, start[k + 1] - start[k]);
+  cudaError_t e = cudaSuccess;
+  if (!h->d_gv_band && (e = dev_malloc(&h->d_gv_band, sizeof(int2) * (size_t)n_rec)) != cudaSuccess) return e;
+  if (!h->d_gv_rows && (e = dev_malloc(&h->d_gv_rows, sizeof(int) * (size_t)(nb + 1))) != cudaSuccess) return e;
+  h->device_bytes += sizeof(int2) * (size_t)n_rec + sizeof(int) * (size_t)(nb + 1);
+  if ((e = cudaMemcpy(h->d_gv_band, band.data(), sizeof(int2) * (size_t)n_rec, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_gv_rows, start.data(), sizeof(int) * (size_t)(nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  long long bytes = 0;
+  for (const int2& x : band) bytes += 4LL * (x.y - x.x);
+  h->gv_blocks = nb;
+  h->gv_max_rows = max_rows;
+  h->gv_bytes = bytes;
+  return cudaSuccess;
 }
 
 void fold_point_init() {
@@ -292,7 +358,8 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
   const double* muref = delta ? h->d_muref64 : nullptr;
   fold_point_kernel<<<fold_point_grid(h), kGvThreads, smem, s>>>(
       h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
-      mu_out, h->d_part, h->d_ticket, out, h->d_status, inject_timeout());
+      mu_out, h->d_part, h->d_ticket, out, h->d_status, inject_timeout(), h->d_gv_band,
+      h->gv_blocks > 0 ? h->d_gv_rows : nullptr);
   return launch_result();
 }
 
@@ -314,7 +381,9 @@ cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* ou
                                            gv_rows_per_block(h), W, muref, (const double*)h->d_n64,
                                            (const double*)h->d_b64, (const unsigned char*)h->d_mask,
                                            (const double*)h->d_cdata, (float*)nullptr, (float*)nullptr, h->d_part,
-                                           h->d_ticket, out, h->d_status, inject_timeout());
+                                           h->d_ticket, out, h->d_status, inject_timeout(),
+                                           (const int2*)h->d_gv_band,
+                                           (const int*)(h->gv_blocks > 0 ? h->d_gv_rows : nullptr));
   return e != cudaSuccess ? e : launch_result();
 }
 
@@ -449,7 +518,7 @@ extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld
   cdata_kernel<<<1, 1024, 0, s>>>(counts, mask, n_rec, &sc->c_data);
   fold_point_kernel<<<grid, kGvThreads, smem, s>>>(R, n_rec, ld, rpb, W, nullptr, counts, bkg, mask, &sc->c_data,
                                                     nullptr, nullptr, sc->parts, &sc->ticket, out, &sc->status,
-                                                    inject_timeout());
+                                                    inject_timeout(), nullptr, nullptr);
   if ((e = launch_result()) != cudaSuccess) {
     g_noalloc_err = cudaGetErrorString(e);
     return SRW_ECUDA;

@@ -1383,6 +1383,7 @@ srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, doub
 srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long n_points, int precision,
                                     double* best_value, long long* best_index, float* ms) {
   if (!s || n_points < 1 || first < 0) return SRW_EINVAL;
+  if (precision != SRW_RANK8 && (precision < SRW_FP32 || precision > SRW_FP16X3)) return SRW_EINVAL;
   cudaStream_t st = s->stream;
   constexpr int kChunk = 65536;
   float4 lo0, w0;
@@ -1404,7 +1405,8 @@ srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long 
     const int cnt = (int)std::min<long long>(kChunk, n_points - off);
     srw::sobol_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(s->d_sobol, first + off, cnt, lo0, lo4, w0, w4, d_th);
     // fixed input and output buffers: the exact path replays one captured graph per chunk size
-    r = srw_loglik(s->h, d_th, cnt, d_o, SRW_DEVICE, (srw_precision)precision, st);
+    r = precision == SRW_RANK8 ? srw_loglik_linear(s->h, d_th, cnt, d_o, nullptr, SRW_DEVICE, st)
+                               : srw_loglik(s->h, d_th, cnt, d_o, SRW_DEVICE, (srw_precision)precision, st);
     if (r == SRW_OK && cudaMemcpyAsync(d_v + off, d_o, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       r = SRW_ECUDA;
   }

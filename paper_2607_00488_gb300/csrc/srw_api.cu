@@ -139,7 +139,7 @@ static void release(srw_ctx* h) {
   dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_nb4); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
-  dfree(h->d_status); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
+  dfree(h->d_status); dfree(h->d_gv_band); dfree(h->d_gv_rows); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
   for (auto& ev : h->ev_fold)
@@ -734,6 +734,10 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
   if (!jr && !h->has_esm_input && !(h->lambda > 0.0))
     return bail(fail(h, SRW_EINVAL, "the SM spectrum folded through R is zero: cannot normalise the exposure"));
 
+  // ---- R on the host once: the GEMV's nonzero bands, the folds' K-block ranges
+  std::vector<float> Rh((size_t)n_rec * h->ld_r);
+  CREATE_CUDA(cudaMemcpy(Rh.data(), h->d_R, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost), "read R");
+  CREATE_CUDA(gemv_prepare(h, Rh), "GEMV bands");
   // ---- tensor-core path: BF16 hi/lo split of R and TMA descriptors
   if (tc_supported(h)) {
     CREATE_CUDA(dalloc(h, &h->d_rhi, (size_t)h->rec_pad * h->k_pad), "alloc R hi");
@@ -752,7 +756,7 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
       }
     }
     CREATE_CUDA(launch_split_r(h, s), "split R");
-    CREATE_CUDA(tc_block_ranges(h, s), "K-block ranges");
+    CREATE_CUDA(tc_block_ranges(h, Rh, s), "K-block ranges");
     CREATE_CUDA(tc_prepare(h), "tensor map encode");
     h->tensor_ok = true;
   }
@@ -1172,6 +1176,13 @@ srw_status srw_fold_work(srw_handle h, srw_precision precision, int tile, double
   *executed_fraction = 1.0;
   if (precision != SRW_FP32 && h->tensor_ok)
     *executed_fraction = tc_block_fraction(h, tile ? tile : h->cfg[precision].bn, precision == SRW_FP16X3);
+  return SRW_OK;
+}
+
+srw_status srw_gemv_work(srw_handle h, long long* bytes) {
+  if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
+  if (!bytes) return fail(h, SRW_EINVAL, "bytes is NULL");
+  *bytes = h->gv_blocks > 0 ? h->gv_bytes : 4LL * h->n_rec * h->ld_r;
   return SRW_OK;
 }
 

@@ -202,6 +202,10 @@ struct srw_ctx {
   int part_cap = 0;
   unsigned* d_ticket = nullptr;
   unsigned* d_status = nullptr;
+  int2* d_gv_band = nullptr;   // [n_rec] single-point GEMV: nonzero band {lo, hi} of each row of R
+  int* d_gv_rows = nullptr;    // [gv_blocks + 1] first row of each GEMV block (band-balanced split)
+  int gv_blocks = 0, gv_max_rows = 0;
+  long long gv_bytes = 0;      // bytes of R the GEMV streams (the bands)
   double* d_bpart = nullptr;   // batched partials [n_tiles][P]
   size_t bpart_cap = 0;
   float* d_theta = nullptr;    // staging for host theta
@@ -292,6 +296,9 @@ cudaError_t launch_set_data(srw_ctx* h, const double* d_bkg, int n_bkg, cudaStre
 cudaError_t launch_data_ref(srw_ctx* h, cudaStream_t s);
 cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s);
 int fold_point_grid(const srw_ctx* h);
+// Nonzero bands of R's rows and the band-balanced row split of the GEMV
+// (R: the device R copied to the host, n_rec x ld_r).
+cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R);
 void fold_point_init();
 int fold_simt_parts(int n_rec);
 cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out, float* mu_out, double* out,
@@ -332,7 +339,7 @@ int tc_max_groups();
 TcGroup tc_group_of(const srw_ctx* h, int bn, bool f16);
 // Per rec tile, the K blocks where the split response has nonzero elements
 // (both splits, both tile widths); blocks outside hold only zeros.
-cudaError_t tc_block_ranges(srw_ctx* h, cudaStream_t s);
+cudaError_t tc_block_ranges(srw_ctx* h, const std::vector<float>& R, cudaStream_t s);
 // Fraction of the (rec tile, K block) pairs a batched fold executes.
 double tc_block_fraction(const srw_ctx* h, int bn, bool f16);
 // Tensor maps of h's hi / lo response (FP16 split if f16, else BF16) with a

@@ -22,6 +22,7 @@ SRW_OK, SRW_EINVAL, SRW_ENOMEM, SRW_ECUDA, SRW_ENODATA, SRW_EDOMAIN, SRW_ETIMEOU
 SRW_HOST, SRW_DEVICE = 0, 1
 SRW_FP32, SRW_BF16, SRW_BF16X3, SRW_FP16X3 = 0, 1, 2, 3
 SRW_SCAN_FLAG_CELLS, SRW_SCAN_ERROR_BARS = 0, 1
+SRW_RANK8 = 16  # srw_surrogate_scan_exact: the exact rank-8 evaluator
 PRECISIONS = {"fp32": SRW_FP32, "bf16": SRW_BF16, "bf16x3": SRW_BF16X3, "fp16x3": SRW_FP16X3}
 
 # Entry points declared in include/srw.h (checked by the test-suite).
@@ -36,7 +37,8 @@ EXPORTS = ("srw_create", "srw_set_data", "srw_spectrum", "srw_spectrum_batch", "
            "srw_diag_wait_timeout", "srw_loglik_linear", "srw_loglik_profiled", "srw_create_joint", "srw_joint_layout",
            "srw_fold_work", "srw_fault_inject", "srw_fault_pending", "srw_fault_parse", "srw_fold_config",
            "srw_set_fold_config", "srw_check", "srw_get_fold_config",
-           "srw_surrogate_save", "srw_surrogate_load", "srw_surrogate_fit_resume", "srw_surrogate_scan_chunked")
+           "srw_surrogate_save", "srw_surrogate_load", "srw_surrogate_fit_resume", "srw_surrogate_scan_chunked",
+           "srw_gemv_work")
 
 
 class SrwError(RuntimeError):
@@ -111,6 +113,7 @@ def lib():
                                        ctypes.POINTER(_JointResponse), ctypes.POINTER(_Options), ctypes.POINTER(vp)]
         L.srw_joint_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.srw_fold_work.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_double)]
+        L.srw_gemv_work.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.srw_set_data.argtypes = [vp, dp, dp, ip, vp]
         L.srw_spectrum.argtypes = [vp, fp, ip, fp, ip, vp]
         L.srw_loglik.argtypes = [vp, fp, ip, vp, ip, ip, vp]
@@ -446,6 +449,13 @@ def srw_set_fold_config(h, precision, index):
     _check(lib().srw_set_fold_config(h, int(precision), int(index)), h)
 
 
+def srw_gemv_work(h):
+    """Bytes of R the single-point GEMV streams per call (its rows' nonzero bands)."""
+    b = ctypes.c_longlong()
+    _check(lib().srw_gemv_work(h, ctypes.byref(b)), h)
+    return b.value
+
+
 def srw_fold_work(h, precision, tile=0):
     """Fraction of the (rec tile, K block) pairs the batched fold executes
     (tile 0: the handle's configured rec-tile width)."""
@@ -769,6 +779,9 @@ class Likelihood:
 
     def layout(self):
         return srw_joint_layout(self.handle)
+
+    def gemv_work(self):
+        return srw_gemv_work(self.handle)
 
     def fold_work(self, precision, tile=0):
         return srw_fold_work(self.handle, precision, tile)

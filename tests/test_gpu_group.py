@@ -13,10 +13,12 @@ one persistent fold launch) through the C ABI.
   mu_hat <= 0.5 (1e5 / E)^(1/4) (the magnetic-moment rate goes as mu_hat^2),
   i.e. the region of the 1e5-event tests scaled to equal Delta(-2 ln L).
   Outside it the model is far from the data (|mu - n| >> sqrt(mu)) and
-  FP32-level per-bin errors alone move -2 ln L by more than 1e-4.  The BF16
-  hi+lo split keeps ~16 significant bits of R and of W - W_ref, an error that
-  grows with the exposure like sqrt(E) at fixed Delta(-2 ln L); its absolute
-  bar applies up to 1e5 events, the budget bound everywhere.
+  FP32-level per-bin errors alone move -2 ln L by more than 1e-4.  The split
+  folds' epilogue forms mu - n from an FP64 constant (b + R W_ref - n), so the
+  FP32 rounding of mu itself (6e-3 at 1e5 counts per bin) no longer enters;
+  the absolute bars are asserted in the fit region at every exposure for FP32
+  and FP16x3, up to 1e5 events for BF16x3 (16 significant bits per operand),
+  the budget bound everywhere.
 * Ragged sizes: configurations with 0, 1 and 129 points, rec-bin counts that
   are not multiples of the tile width, true-bin counts that are not multiples
   of the K block.
@@ -192,8 +194,11 @@ def _check_vs_oracle(srw, members, got_by_member, prec, idx_fn):
             e = _eval_budget(m, th, prec)
             worst.append((d, b, fit, m.wl["exposure"], m.wl["name"], i))
             assert d <= TOL[prec] + 2.0 * b + e, (m.wl["name"], i, d, b, e)
-            if fit and (prec == 0 or m.wl["exposure"] <= 1e5):
-                assert d <= TOL[prec], (m.wl["name"], i, d, b)
+            # the exposure-scaled fit region: FP32 and FP16x3 at every exposure (1e4 - 1e7
+            # events); BF16x3 (16-bit operands, an error growing like sqrt(E) at fixed
+            # Delta(-2 ln L)) up to 1e5 events, where it measured 2.4e-3 at 1e6
+            if fit and (prec != 2 or m.wl["exposure"] <= 1e5):
+                assert d <= TOL[prec], (m.wl["name"], i, d, b, m.wl["exposure"])
     return worst
 
 

@@ -478,3 +478,26 @@ def test_fold_candidates_are_bitwise_equal(srw, solar):
             np.testing.assert_array_equal(got[0], ref[0], err_msg="candidate %d" % i)
             np.testing.assert_allclose(got[1], ref[1], rtol=1e-12, atol=1e-9, err_msg="candidate %d" % i)
         solar.lk.set_fold_config(prec, 0)
+
+
+def _band_bytes(R, ld):
+    """Host recomputation of the GEMV's streamed columns: per row the first
+    nonzero column rounded down to 4 floats, the length rounded up to 32 floats
+    and kept inside the padded row; an all-zero row keeps 32."""
+    total = 0
+    for row in np.asarray(R, np.float32):
+        nz = np.nonzero(row)[0]
+        if nz.size == 0:
+            total += 32
+            continue
+        lo = nz[0] // 4 * 4
+        total += min(ld, -(-(nz[-1] + 1 - lo) // 32) * 32)
+    return 4 * total
+
+
+@pytest.mark.parametrize("name", ["be7", "solar"])
+def test_gemv_streams_the_nonzero_bands(srw, name, request):
+    c = request.getfixturevalue(name)
+    ld = c.lk.info()["k_pad"]
+    assert c.lk.gemv_work() == _band_bytes(c.wl["R"], ld)
+    assert c.lk.gemv_work() < 4 * c.wl["R"].size  # the banded response leaves part of every row empty
