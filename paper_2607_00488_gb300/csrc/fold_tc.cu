@@ -252,7 +252,11 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   constexpr int kShatSlots = KS::kShatSlots;
   constexpr int kShatBytes = KS::kShatBytes;
   extern __shared__ unsigned char dsmem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsmem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base for the swizzled tiles, formed by pointer arithmetic on
+  // the shared array so that plain loads through it stay shared-memory loads
+  // (a round trip through an integer makes them generic loads: slower, and on
+  // the long scoreboard)
+  unsigned char* smem = dsmem_raw + ((1024u - (ptx::smem_addr(dsmem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t r_full[ST], w_full[ST], empty[ST], acc_full[NB], acc_empty[NB], drain;
   __shared__ __align__(8) uint64_t s_full[kShatSlots], s_empty[kShatSlots], never;
   __shared__ uint32_t tmem_slot;
@@ -345,8 +349,8 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         const int st = g % ST, sl = g % kShatSlots;
         // the A buffers of this stage are free once the MMAs of its previous
         // use have completed; the coefficient spectra come through their own ring
-        if (!warp_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 64) ||
-            !warp_wait(&s_full[sl], (g / kShatSlots) & 1, &abort_flag, 64)) {
+        if (!warp_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag) ||
+            !warp_wait(&s_full[sl], (g / kShatSlots) & 1, &abort_flag)) {
           give_up();
           ok = false;
           break;
@@ -414,7 +418,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const int buf = tc % NB;
       const int p = m0 + q * 32 + lane;
       if (!dead && __any_sync(0xffffffffu, aborted(&abort_flag))) dead = true;
-      if (!dead && !warp_wait(&acc_full[buf], (tc / NB) & 1, &abort_flag, 256)) {
+      if (!dead && !warp_wait(&acc_full[buf], (tc / NB) & 1, &abort_flag)) {
         give_up();
         dead = true;
       }
@@ -504,7 +508,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
           const int kb = kb_at<BK>(kr, kk);
           const int st = g % ST;
-          if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
+          if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag)) {
             give_up();
             ok = false;
             break;
@@ -531,7 +535,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
           const int kb = kb_at<BK>(kr, kk);
           const int sl = g % kShatSlots;
-          if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
+          if (!ptx::mbar_wait(&s_empty[sl], ((g / kShatSlots) & 1) ^ 1, &abort_flag)) {
             give_up();
             ok = false;
             break;

@@ -108,7 +108,11 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
   using S = GemmShape<BN>;
   constexpr int ST = S::kStages;
   extern __shared__ unsigned char dsmem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsmem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base for the swizzled tiles, formed by pointer arithmetic on
+  // the shared array so that plain loads through it stay shared-memory loads
+  // (a round trip through an integer makes them generic loads: slower, and on
+  // the long scoreboard)
+  unsigned char* smem = dsmem_raw + ((1024u - (ptx::smem_addr(dsmem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full[ST], empty[ST], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ unsigned abort_flag;
@@ -152,7 +156,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
         const int m0 = (t / n_tn) * kBM, n0 = (t % n_tn) * BN;
         for (int kb = 0; kb < n_kb; ++kb, ++g) {
           const int st = g % ST;
-          if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag, 2000000000ull, 32)) {
+          if (!ptx::mbar_wait(&empty[st], ((g / ST) & 1) ^ 1, &abort_flag)) {
             give_up();
             ok = false;
             break;
@@ -215,7 +219,7 @@ mlp_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant
       if (__any_sync(0xffffffffu, aborted(&abort_flag))) break;
       const int m0 = (t / n_tn) * kBM, n0 = (t % n_tn) * BN;
       const int buf = tc & 1;
-      if (!warp_wait(&acc_full[buf], (tc >> 1) & 1, &abort_flag, 128)) {
+      if (!warp_wait(&acc_full[buf], (tc >> 1) & 1, &abort_flag)) {
         give_up();
         break;
       }

@@ -46,28 +46,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not yet complete
+// is suspended by the hardware until the phase completes or about `hint_ns`
+// nanoseconds have passed, without issuing polling instructions meanwhile.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for phase `parity` of `bar` to complete.  Gives up after about
 // `limit_ns` (measured on the SM cycle counter, assuming ~2 GHz) or when
-// *abort becomes non-zero (another role gave up); returns false then.  The
-// clock and the abort flag are consulted only every 1024 polls (every 16
-// with a back-off), so a wait that succeeds soon costs no clock reads.
-// sleep_ns > 0 backs off between polls (for waits that are expected to be
-// long, so that the waiting warp does not take issue slots from others).
+// *abort becomes non-zero (another role gave up); returns false then.  Each
+// retry suspends the thread in hardware for up to 20 us (woken as soon as the
+// phase completes), so a waiting warp takes almost no issue slots from the
+// warps that compute; the abort flag and the clock are checked between
+// retries.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile unsigned* abort,
-                                          uint64_t limit_ns = 2000000000ull, unsigned sleep_ns = 0) {
+                                          uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
-  const uint32_t check_mask = sleep_ns ? 15u : 1023u;
   const long long limit_cycles = (long long)(limit_ns * 2ull);
-  long long t0 = -1;
-  for (uint32_t it = 1;; ++it) {
-    if (sleep_ns) __nanosleep(sleep_ns);
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & check_mask) == 0) {
-      if (abort != nullptr && *abort != 0u) return false;
-      const long long now = clock64();
-      if (t0 < 0) t0 = now;
-      else if (now - t0 > limit_cycles) return false;
-    }
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+    if (abort != nullptr && *abort != 0u) return false;
+    if (clock64() - t0 > limit_cycles) return false;
   }
 }
 

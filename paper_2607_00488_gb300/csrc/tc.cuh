@@ -124,9 +124,8 @@ __device__ __forceinline__ bool aborted(const unsigned* f) { return *(const vola
 // Bounded wait taken by all 32 lanes of a warp; the warp proceeds only if
 // every lane saw the phase complete, so no lane can run ahead into a
 // .sync.aligned instruction or a __syncwarp that the others skip.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, unsigned* abort_flag,
-                                          unsigned sleep_ns = 0) {
-  const bool ok = ptx::mbar_wait(bar, parity, abort_flag, 2000000000ull, sleep_ns);
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, unsigned* abort_flag) {
+  const bool ok = ptx::mbar_wait(bar, parity, abort_flag);
   return __all_sync(0xffffffffu, ok);
 }
 
