@@ -20,10 +20,10 @@
 //              bin), evaluates the Poisson terms with the mask multiplied out
 //              and accumulates them per point (double-float), one FP64 partial
 //              per (rec tile, point).
-//   warp 12    TMA producers: lane 0 streams R hi (+ lo) tiles, 64 x BN,
-//              128-byte swizzle; lane 1 streams the 2 KB coefficient-spectra
-//              slice of each K block, up to kShatSlots blocks ahead.
+//   warp 12    TMA producer: streams R hi (+ lo) tiles, BK x BN, swizzled.
 //   warp 13    MMA issuer (one thread) and TMEM owner.
+//   warp 14    TMA producer of the coefficient-spectra slice of each K block
+//              (BK x 8 floats), up to kShatSlots blocks ahead.
 //
 // The fold is taken of W(theta) - W_ref (the reference point's FP64 fold
 // R W_ref enters the epilogue with the background), so the BF16 rounding
@@ -72,7 +72,8 @@ constexpr int kWWarps = 8;
 constexpr int kEpiWarp0 = 8;
 constexpr int kTmaWarp = 12;
 constexpr int kMmaWarp = 13;
-constexpr int kThreads = 14 * 32;
+constexpr int kShatWarp = 14;
+constexpr int kThreads = 15 * 32;
 
 // Pipeline stage of BK true bins (BK = 64: rows of 128 bytes, 128-byte
 // swizzle; BK = 32: rows of 64 bytes, 64-byte swizzle, twice the stages in
@@ -193,8 +194,12 @@ struct TcLaunch {
   const TcGroup* groups;       // grouped: one per configuration (nullptr: single)
   const int4* items;           // grouped: slot k * gridDim.x + b = {group, m0, n0, 0}, CTA b's k-th item
   int n_items;                 // single: m_tiles x n_tiles; grouped: slots
-  const float* theta;          // [points][5]; a group's points start at p_off
-  const float* wscale;         // SRW_FP16X3: per-point scales s_p (indexed like theta)
+  // per point (a group's points start at p_off) two float4: {c0, c1, c2, c3}
+  // and {c4, c5, c7, s}, the seven point-dependent coupling coefficients
+  // (the constant monomial c6 is always in the reference fold) times the
+  // point's power-of-two scale s, and s itself (1 unless SRW_FP16X3); written
+  // by coef_kernel / group_coef_kernel
+  const float4* coef;
   double* parts;
   float* musig_out;            // single configuration only: [P][n_rec] folded deviations
   unsigned* status;
@@ -323,25 +328,21 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       int m0, n0, gi;
       const TcGroup G = work_at<GROUPED, BN>(L, idx, m0, n0, gi);
       if (GROUPED && gi < 0) break;  // stop item: this CTA's list is done
-      const float* theta = L.theta + (size_t)G.p_off * 5;
-      const dfloat s2w = {G.sin2w_hi, G.sin2w_lo};
       // K blocks of this rec tile that hold nonzero response (the rest add exact zeros)
       const int2 kr = tile_walk<GROUPED, BN>(G, n0);
-      float c[4][kNB];
+      // the coefficients of this thread's four points, computed once per point
+      // by the pre-pass (not once per W warp and item)
+      float c[4][kNB - 1];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int p = m0 + rg + 32 * rr;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
         if (p < G.P) {
-          coefficients(theta + (size_t)p * 5, s2w, G.cref, c[rr]);
-          if (F16) {  // the point's power-of-two scale, exact in every product and sum
-            const float sc = L.wscale[(size_t)G.p_off + p];
-#pragma unroll
-            for (int b = 0; b < kNB; ++b) c[rr][b] *= sc;
-          }
-        } else {
-#pragma unroll
-          for (int b = 0; b < kNB; ++b) c[rr][b] = 0.f;
+          a = __ldg(L.coef + 2 * ((size_t)G.p_off + p));
+          b = __ldg(L.coef + 2 * ((size_t)G.p_off + p) + 1);
         }
+        c[rr][0] = a.x; c[rr][1] = a.y; c[rr][2] = a.z; c[rr][3] = a.w;
+        c[rr][4] = b.x; c[rr][5] = b.y; c[rr][6] = b.z;
       }
       bool ok = true;
       for (int kk = 0; kk < kb_count<BK>(kr); ++kk, ++g) {
@@ -369,7 +370,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
               float a = c[rr][0] * sv[0];
 #pragma unroll
               for (int bb = 1; bb < kNB; ++bb)  // the constant monomial (6) is always in the reference fold
-                if (bb != 6) a = fmaf(c[rr][bb], sv[bb], a);
+                if (bb != 6) a = fmaf(c[rr][bb < 6 ? bb : 6], sv[bb], a);
               w[rr][e] = a;
             }
           }
@@ -431,7 +432,7 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * S::kAccCols);
       float sinv = 1.f;  // 1 / s_p (exact: s_p is a power of two)
-      if (F16 && p < P) sinv = 1.f / L.wscale[(size_t)G.p_off + p];
+      if (F16 && p < P) sinv = 1.f / __ldg(L.coef + 2 * ((size_t)G.p_off + p) + 1).w;
       dfloat acc = {0.f, 0.f};
       bool infinite = false;  // a +inf term (mu <= 0 with data) is kept apart: TwoSum would make it NaN
       float mneg = 0.f;       // smallest mu of the active bins (below 0: outside the domain)
@@ -523,7 +524,12 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       // never end with copies in flight
       for (int u = max(0, issued_g - ST); u < issued_g; ++u)
         ptx::mbar_wait(&r_full[u % ST], (u / ST) & 1, nullptr, 100000000ull);
-    } else if (lane == 1) {  // coefficient-spectra slices, up to kShatSlots blocks ahead
+    }
+  } else if (warp == kShatWarp) {
+    // ------------------------------------------------------------ coefficient spectra
+    // its own warp: a lane of the R producer's warp would share that warp's
+    // (mostly suspended) instruction stream
+    if (lane == 0) {  // one 2 KB slice per K block, up to kShatSlots blocks ahead
       int g = 0, issued = 0;
       bool ok = true;
       FOR_ITEMS(idx) {
@@ -656,28 +662,36 @@ __global__ void split_r16_kernel(const float* __restrict__ R, int n_rec, int ld,
   }
 }
 
-// Per-point FP16 scales s_p from the bound sum_b |c_b - c_b,ref| max_i |shat_b,i|
-// of the weighted-spectrum deviations (FP32 products and sums without
-// contraction, so every caller gets the same power of two).
-__device__ __forceinline__ float wscale_of(const float* th, const TcGroup& G) {
+// Per-point coefficients of the W producers.  The FP16 scale s_p is the power
+// of two of the bound sum_b |c_b - c_b,ref| max_i |shat_b,i| of the weighted-
+// spectrum deviations (FP32 products and sums without contraction, so every
+// caller gets the same power of two); the BF16 splits use s_p = 1.
+__device__ __forceinline__ void point_coef(const float* th, const TcGroup& G, bool f16, float4* out) {
   float c[kNB];
   coefficients(th, dfloat{G.sin2w_hi, G.sin2w_lo}, G.cref, c);
-  float bound = 0.f;
+  float sc = 1.f;
+  if (f16) {
+    float bound = 0.f;
 #pragma unroll
-  for (int b = 0; b < kNB; ++b) bound = __fadd_rn(bound, __fmul_rn(fabsf(c[b]), G.wmax[b]));
-  return pow2_scale(bound);
+    for (int b = 0; b < kNB; ++b) bound = __fadd_rn(bound, __fmul_rn(fabsf(c[b]), G.wmax[b]));
+    sc = pow2_scale(bound);
+  }
+  // exact: sc is a power of two
+  out[0] = make_float4(c[0] * sc, c[1] * sc, c[2] * sc, c[3] * sc);
+  out[1] = make_float4(c[4] * sc, c[5] * sc, c[7] * sc, sc);
 }
 
-__global__ void wscale_kernel(const TcGroup g0, const float* __restrict__ theta, float* __restrict__ out) {
+__global__ void coef_kernel(const TcGroup g0, const float* __restrict__ theta, int f16, float4* __restrict__ out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < g0.P) out[p] = wscale_of(theta + (size_t)p * 5, g0);
+  if (p < g0.P) point_coef(theta + (size_t)p * 5, g0, f16 != 0, out + 2 * (size_t)p);
 }
 
-__global__ void group_wscale_kernel(const TcGroup* __restrict__ groups, const float* __restrict__ theta,
-                                    float* __restrict__ out) {
+__global__ void group_coef_kernel(const TcGroup* __restrict__ groups, const float* __restrict__ theta, int f16,
+                                  float4* __restrict__ out) {
   const TcGroup G = groups[blockIdx.y];
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < G.P) out[(size_t)G.p_off + p] = wscale_of(theta + ((size_t)G.p_off + p) * 5, G);
+  if (p < G.P)
+    point_coef(theta + ((size_t)G.p_off + p) * 5, G, f16 != 0, out + 2 * ((size_t)G.p_off + p));
 }
 
 __global__ void shat_k8_kernel(const float* __restrict__ shat, int k_pad, float* __restrict__ out) {
@@ -983,20 +997,17 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   L.groups = nullptr;
   L.items = nullptr;
   L.n_items = ((P + kBM - 1) / kBM) * L.g0.n_tiles;
-  L.theta = theta;
-  L.wscale = f16 ? h->d_wscale : nullptr;
+  L.coef = h->d_coef;
   L.parts = parts;
   L.musig_out = musig_out;
   L.status = h->d_status;
   L.inject = inject_timeout();
   if (n_parts) *n_parts = L.g0.n_tiles;
-  if (f16) {
-    if (h->d_wscale == nullptr || h->wscale_cap < P) return cudaErrorInvalidValue;
-    wscale_kernel<<<(P + 255) / 256, 256, 0, s>>>(L.g0, theta, h->d_wscale);
-  }
+  if (h->d_coef == nullptr || h->coef_cap < P) return cudaErrorInvalidValue;
+  coef_kernel<<<(P + 255) / 256, 256, 0, s>>>(L.g0, theta, f16 ? 1 : 0, h->d_coef);
   const int grid = L.n_items < h->sm_count ? L.n_items : h->sm_count;
   cudaError_t e;
-  // optional events around the fold kernel alone (not the scale pre-pass)
+  // optional events around the fold kernel alone (not the coefficient pre-pass)
   if (ev_begin && (e = cudaEventRecord(ev_begin, s)) != cudaSuccess) return e;
   const int bk = cfg.bk == 32 ? 32 : 64, ki = bk == 32 ? 1 : 0;
   e = launch_single(bn, bk, precision, f16 ? maps->hi16[ki][bi] : maps->hi[ki][bi],
@@ -1005,23 +1016,22 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   return e;
 }
 
-cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
-                                cudaStream_t s) {
+cudaError_t launch_group_coef(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, bool f16,
+                              float4* out, cudaStream_t s) {
   if (n_groups < 1 || max_P < 1) return cudaSuccess;
-  group_wscale_kernel<<<dim3((max_P + 255) / 256, n_groups), 256, 0, s>>>(d_groups, theta, out);
+  group_coef_kernel<<<dim3((max_P + 255) / 256, n_groups), 256, 0, s>>>(d_groups, theta, f16 ? 1 : 0, out);
   return launch_result();
 }
 
 cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_groups, const int4* d_items, int n_slots,
-                                 int n_cta, const float* theta, const float* wscale, double* parts, unsigned* status,
+                                 int n_cta, const float4* coef, double* parts, unsigned* status,
                                  cudaStream_t s) {
   if (n_cta < 1) return cudaSuccess;
   TcLaunch L{};
   L.groups = d_groups;
   L.items = d_items;
   L.n_items = n_slots;
-  L.theta = theta;
-  L.wscale = wscale;
+  L.coef = coef;
   L.parts = parts;
   L.musig_out = nullptr;
   L.status = status;

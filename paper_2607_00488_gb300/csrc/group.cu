@@ -85,7 +85,7 @@ struct srw_group_ctx {
   size_t simt_parts = 0;
   double* d_parts = nullptr;
   size_t parts_cap = 0;
-  float* d_wscale = nullptr;        // per-point FP16 scales (SRW_FP16X3)
+  float4* d_coef = nullptr;         // [points][2] W-producer coefficients and FP16 scales
   float* d_theta = nullptr;         // staging for host calls
   double* d_out = nullptr;
   unsigned* d_status = nullptr;
@@ -314,11 +314,11 @@ srw_status run(srw_group g, const float* th, double* o, int precision, cudaStrea
   }
   srw_status st = ensure_parts(g, pl.n_parts);
   if (st != SRW_OK) return st;
-  if (precision == SRW_FP16X3)
-    G_CUDA(g, srw::launch_group_wscale(pl.d_groups, g->n, g->P_max, th, g->d_wscale, s), "FP16 scales");
+  G_CUDA(g, srw::launch_group_coef(pl.d_groups, g->n, g->P_max, th, precision == SRW_FP16X3, g->d_coef, s),
+         "point coefficients");
   if (g->profile) G_CUDA(g, cudaEventRecord(g->ev[0], s), "event");
-  G_CUDA(g, srw::launch_fold_tc_group(pl.bn_max, precision, pl.d_groups, pl.d_items, pl.n_slots, pl.n_cta, th,
-                                      precision == SRW_FP16X3 ? g->d_wscale : nullptr, g->d_parts, g->d_status, s),
+  G_CUDA(g, srw::launch_fold_tc_group(pl.bn_max, precision, pl.d_groups, pl.d_items, pl.n_slots, pl.n_cta, g->d_coef,
+                                      g->d_parts, g->d_status, s),
          "grouped fold");
   if (g->profile) G_CUDA(g, cudaEventRecord(g->ev[1], s), "event");
   G_CUDA(g, srw::launch_group_reduce(pl.d_gparts, g->n, g->P_max, g->d_parts, o, g->d_status, s), "reduce");
@@ -372,7 +372,7 @@ srw_status srw_group_create(const srw_handle* handles, int n, const int* P, srw_
   if (e == cudaSuccess) e = srw::dev_malloc(&g->d_status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = srw::dev_malloc(&g->d_theta, sizeof(float) * 5 * total);
-  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_wscale, sizeof(float) * total);
+  if (e == cudaSuccess) e = srw::dev_malloc(&g->d_coef, 2 * sizeof(float4) * total);
   if (e == cudaSuccess) e = srw::dev_malloc(&g->d_out, sizeof(double) * total);
   if (e != cudaSuccess) {
     srw_group_destroy(g);
@@ -552,7 +552,7 @@ srw_status srw_group_destroy(srw_group g) {
   invalidate(g);
   gfree(g->d_parts);
   gfree(g->d_theta);
-  gfree(g->d_wscale);
+  gfree(g->d_coef);
   gfree(g->d_out);
   gfree(g->d_status);
   for (auto& ev : g->ev)

@@ -136,7 +136,7 @@ static void release(srw_ctx* h) {
   dfree(h->d_bin_l); dfree(h->d_bin64); dfree(h->d_basis); dfree(h->d_ssm64); dfree(h->d_esm64);
   for (int f = 0; f < 2; ++f)
     for (int b = 0; b < 2; ++b) dfree(h->d_kbr[f][b]);
-  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_wscale); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
+  dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_coef); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_nb4); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
   dfree(h->d_status); dfree(h->d_gv_band); dfree(h->d_gv_rows); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
@@ -171,14 +171,14 @@ static srw_status ensure_staging(srw_ctx* h, int P) {
   return SRW_OK;
 }
 
-// Per-point scale buffer of the FP16 split.
-static srw_status ensure_wscale(srw_ctx* h, int P) {
-  if (P <= h->wscale_cap) return SRW_OK;
-  const int cap = std::max(P, 2 * h->wscale_cap);
+// Per-point coefficient buffer of the tensor-core folds (two float4 a point).
+static srw_status ensure_coef(srw_ctx* h, int P) {
+  if (P <= h->coef_cap) return SRW_OK;
+  const int cap = std::max(P, 2 * h->coef_cap);
   destroy_graphs(h);
-  dfree(h->d_wscale);
-  SRW_CUDA(h, dev_malloc(&h->d_wscale, sizeof(float) * (size_t)cap), "FP16 scales");
-  h->wscale_cap = cap;
+  dfree(h->d_coef);
+  SRW_CUDA(h, dev_malloc(&h->d_coef, 2 * sizeof(float4) * (size_t)cap), "point coefficients");
+  h->coef_cap = cap;
   return SRW_OK;
 }
 
@@ -955,7 +955,7 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
     } else {
       const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
       st = ensure_bparts(h, (size_t)n_parts_max * P);
-      if (st == SRW_OK && precision == SRW_FP16X3) st = ensure_wscale(h, P);
+      if (st == SRW_OK && precision != SRW_FP32) st = ensure_coef(h, P);
       if (st != SRW_OK) return st;
       int n_parts = 0;
       cudaError_t e = cudaSuccess;
@@ -982,7 +982,7 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   } else {
     const int n_parts_max = precision == SRW_FP32 ? fold_simt_parts(h->n_rec) : (h->rec_pad / 128);
     st = ensure_bparts(h, (size_t)n_parts_max * P);
-    if (st == SRW_OK && precision == SRW_FP16X3) st = ensure_wscale(h, P);
+    if (st == SRW_OK && precision != SRW_FP32) st = ensure_coef(h, P);
     if (st != SRW_OK) return st;
     const FoldConfig cfg = h->cfg[precision];
     st = run_graph(h, 2, precision, P, th, o, s, [&](cudaStream_t cs) {
@@ -1122,8 +1122,8 @@ srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* ou
   const float* th = theta;
   float* o = out;
   float* d_tmp = nullptr;
-  if (precision == SRW_FP16X3) {
-    srw_status st = ensure_wscale(h, P);
+  if (precision != SRW_FP32) {
+    srw_status st = ensure_coef(h, P);
     if (st != SRW_OK) return st;
   }
   if (where == SRW_HOST) {
@@ -1235,7 +1235,7 @@ srw_status srw_autotune(srw_handle h, int P, srw_precision precision, const char
   if (st != SRW_OK) return st;
   const int n_parts_max = h->rec_pad / 128;
   st = ensure_bparts(h, (size_t)n_parts_max * P);
-  if (st == SRW_OK && pr == SRW_FP16X3) st = ensure_wscale(h, P);
+  if (st == SRW_OK) st = ensure_coef(h, P);
   if (st != SRW_OK) return st;
   // deterministic in-box points for timing
   std::vector<float> th((size_t)P * 5);

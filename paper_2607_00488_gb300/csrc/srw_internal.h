@@ -178,11 +178,11 @@ struct srw_ctx {
   int2* d_kbr[2][2] = {};          // [FP16 split?][bn == 256] K-block range of each rec tile
   std::vector<int2> kbr_h[2][2];   // host copies (grouped scheduling, work accounting)
   float wmax[8] = {};              // max_i |shat_b,i|
-  float* d_wscale = nullptr;       // [P] per-point scales of the FP16 split (batched scratch)
+  float4* d_coef = nullptr;        // [P][2] per-point W-producer coefficients and FP16 scales (batched scratch)
   double* d_linM = nullptr;        // [n_rec][8] M = R shat^T (FP64) of the rank-8 evaluator
   float4* d_lin = nullptr;         // [3 n_rec] per-bin constants of the rank-8 evaluator
   float4* d_linp = nullptr;        // [n_rec] {mu_ref, b, n, 0} for the profiled evaluation
-  int wscale_cap = 0;
+  int coef_cap = 0;
 
   // data
   double* d_n64 = nullptr;
@@ -331,7 +331,8 @@ cudaError_t launch_linear_loglik(const srw_ctx* h, const float* theta, int P, do
 cudaError_t launch_linear_profiled(const srw_ctx* h, const float* theta, int P, double sigma_alpha, double* out,
                                    double* alpha, cudaStream_t s);
 // Per-point power-of-two scales of the FP16 split for a grouped launch.
-cudaError_t launch_group_wscale(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, float* out,
+cudaError_t launch_group_coef(const TcGroup* d_groups, int n_groups, int max_P, const float* theta, bool f16,
+                              float4* out,
                                 cudaStream_t s);
 int tc_max_groups();
 // Descriptor of handle h as a configuration with rec tile bn (maps left null)
@@ -350,7 +351,7 @@ cudaError_t tc_encode_maps(const srw_ctx* h, int bn, bool f16, CUtensorMap* hi, 
 // n0, 0}; a group < 0 ends that CTA's list.  bn_max (128 or 256) bounds every
 // group's bn.
 cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_groups, const int4* d_items, int n_slots,
-                                 int n_cta, const float* theta, const float* wscale, double* parts, unsigned* status,
+                                 int n_cta, const float4* coef, double* parts, unsigned* status,
                                  cudaStream_t s);
 // -2 ln L of every point of a grouped call from its per-tile partial sums.
 cudaError_t launch_group_reduce(const GroupPart* d_gparts, int n_groups, int max_P, const double* parts,
