@@ -33,16 +33,45 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---------------------------------------------------------------------------
 // One block per SM owns a contiguous range of rows.  A producer warp streams
-// R in chunks of up to 16 KB into a kGvStages-deep ring; eight consumer warps
-// each take one eighth of every chunk, multiply by W (read through L1), keep
-// FP32 partial sums per chunk and fold them into an FP64 per-lane
-// accumulator.  A consumer warp releases a stage with one arrive.  Every wait
-// is bounded (see ptx.cuh); a block that gives up raises kStatusTimeout.
+// the rows' nonzero bands into a kGvStages-deep ring of 16 KB stages (several
+// short bands share a stage, in a segment table built at create); the rows
+// are dealt in turn to eight consumer warps, which multiply them by W (read
+// through L1), keep FP32 partial sums over at most eight float4 a lane and
+// fold them into a double-float per-lane accumulator; each lane leaves its
+// share of a row in shared memory and the epilogue adds the 32 shares.  Every
+// consumer warp releases every stage with one arrive.  Every wait is bounded
+// (see ptx.cuh); a block that gives up raises kStatusTimeout.
 // ---------------------------------------------------------------------------
 constexpr int kGvConsumers = 8;
 constexpr int kGvThreads = (kGvConsumers + 1) * 32;
 constexpr int kGvChunk = 4096;  // floats per stage (16 KB)
 constexpr int kGvStages = 6;
+constexpr int kGvRowCost = 1024;  // floats: the fixed cost of one row's copy, see gemv_prepare
+
+// One segment of a block's stream: `len` floats (a multiple of 32) of the
+// block's row `row` from column k0, at float offset `off` of the block's ring
+// stage number `stage`; `done` marks the row's last segment.  Segments come
+// in stage order, and the segments of a row are consecutive.
+struct GvSeg {
+  int row, k0, len, off, stage;
+  bool done;
+};
+
+// Create-time table entry {row | done << 30, k0, len, off | stage << 16}.
+__device__ __forceinline__ GvSeg gv_unpack(int4 v) {
+  return {v.x & 0x3fffffff, v.y, v.z, v.w & 0xffff, v.w >> 16, ((v.x >> 30) & 1) != 0};
+}
+
+// Without a table every row is streamed whole, cut into chunk-sized
+// segments, one segment per stage.
+__device__ __forceinline__ GvSeg gv_dense(int i, int ld, int chunk) {
+  const int per_row = (ld + chunk - 1) / chunk, part = i % per_row, k0 = part * chunk;
+  return {i / per_row, k0, min(chunk, ld - k0), 0, i, part == per_row - 1};
+}
+
+// Row stride of the per-lane row partials [lane][row]: odd, so that the 32
+// lanes of a warp write to different banks.
+__host__ __device__ constexpr int gv_part_stride(int rows) { return rows | 1; }
 
 __global__ void __launch_bounds__(kGvThreads, 1)
 fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_block, const float* __restrict__ W,
@@ -50,11 +79,14 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
                   const unsigned char* __restrict__ mask, const double* __restrict__ c_data,
                   float* __restrict__ musig_out, float* __restrict__ mu_out, double* __restrict__ parts,
                   unsigned* __restrict__ ticket, double* __restrict__ out, unsigned* __restrict__ status,
-                  int inject, const int2* __restrict__ band, const int* __restrict__ row_start) {
+                  int inject, const int4* __restrict__ seg, const int* __restrict__ seg_start,
+                  const int* __restrict__ row_start) {
   extern __shared__ __align__(128) unsigned char dsmem[];
   const int chunk = ld < kGvChunk ? ld : kGvChunk;
+  const int ps = gv_part_stride(rows_per_block);
   float* sbuf = reinterpret_cast<float*>(dsmem);
   float2* spart = reinterpret_cast<float2*>(dsmem + sizeof(float) * (size_t)kGvStages * chunk);
+  int4* sseg = reinterpret_cast<int4*>(spart + (size_t)32 * ps);
   __shared__ __align__(8) uint64_t full[kGvStages], empty[kGvStages], never;
   __shared__ unsigned abort_flag;
   __shared__ double sred[kGvThreads / 32];
@@ -66,10 +98,15 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   const int r0 = row_start ? row_start[blockIdx.x] : blockIdx.x * rows_per_block;
   const int r1 = row_start ? row_start[blockIdx.x + 1] : min(n_rec, r0 + rows_per_block);
   const int nrows = r1 > r0 ? r1 - r0 : 0;
-  // columns of row r that are streamed: its nonzero band (a multiple of 32
-  // floats, 16-byte aligned), else the whole padded row; outside the band
-  // every element of R is an exact zero, so skipping it changes nothing
-  auto row_band = [&](int r) { return band ? band[r] : make_int2(0, ld); };
+  // the block's segments: from the create-time table (each row's nonzero
+  // band, outside which R is exactly zero, short bands packed several to a
+  // stage), staged in shared memory so that no walk waits on global memory;
+  // else whole padded rows
+  const int s0 = seg ? seg_start[blockIdx.x] : 0;
+  const int nseg = seg ? seg_start[blockIdx.x + 1] - s0 : nrows * ((ld + chunk - 1) / chunk);
+  if (seg)
+    for (int i = threadIdx.x; i < nseg; i += blockDim.x) sseg[i] = seg[s0 + i];
+  auto seg_at = [&](int i) { return seg ? gv_unpack(sseg[i]) : gv_dense(i, ld, chunk); };
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kGvStages; ++st) {
@@ -83,27 +120,33 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   __syncthreads();
 
   if (warp == kGvConsumers) {
-    // ---- producer (one lane)
+    // ---- producer (one lane): every segment posts its bytes and its copy;
+    // one arrive closes a stage
     if (lane == 0) {
-      int issued = 0, u = 0;
+      int cur = -1;
       bool ok = true;
-      for (int row = r0; row < r1 && ok; ++row) {
-        const int2 b = row_band(row);
-        for (int k0 = b.x; k0 < b.y; k0 += chunk, ++u) {
-          const int st = u % kGvStages;
-          if (u >= kGvStages && !ptx::mbar_wait(&empty[st], ((u / kGvStages) - 1) & 1, &abort_flag)) {
+      for (int i = 0; i < nseg; ++i) {
+        const GvSeg g = seg_at(i);
+        if (g.stage != cur) {
+          if (cur >= 0) ptx::mbar_arrive(&full[cur % kGvStages]);
+          cur = g.stage;
+          if (cur >= kGvStages &&
+              !ptx::mbar_wait(&empty[cur % kGvStages], ((cur / kGvStages) - 1) & 1, &abort_flag)) {
             atomicExch(&abort_flag, 1u);
             atomicOr(status, kStatusTimeout);
             ok = false;
             break;
           }
-          const int len = min(chunk, b.y - k0);
-          SRW_CHECK(status, row < n_rec && k0 >= 0 && len > 0 && k0 + len <= ld && (len & 31) == 0);
-          ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)len * 4u);
-          ptx::bulk_g2s(sbuf + (size_t)st * chunk, R + (size_t)row * ld + k0, (uint32_t)len * 4u, &full[st]);
-          issued = u + 1;
         }
+        SRW_CHECK(status, g.row >= 0 && g.row < nrows && g.k0 >= 0 && g.len > 0 && g.k0 + g.len <= ld &&
+                              (g.len & 31) == 0 && g.off >= 0 && g.off + g.len <= chunk);
+        const int st = cur % kGvStages;
+        ptx::mbar_expect_tx(&full[st], (uint32_t)g.len * 4u);
+        ptx::bulk_g2s(sbuf + (size_t)st * chunk + g.off, R + (size_t)(r0 + g.row) * ld + g.k0, (uint32_t)g.len * 4u,
+                      &full[st]);
       }
+      if (ok && cur >= 0) ptx::mbar_arrive(&full[cur % kGvStages]);
+      const int issued = ok ? cur + 1 : cur;  // stages whose copies were all posted
       // never let the block end with copies in flight
       for (int u = max(0, issued - kGvStages); u < issued; ++u)
         ptx::mbar_wait(&full[u % kGvStages], (u / kGvStages) & 1, nullptr, 100000000ull);
@@ -122,25 +165,38 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
       atomicOr(status, kStatusTimeout);
     }
     dfloat lacc = {0.f, 0.f};
-    int u = 0;
+    int cur = -1;
     bool ok = true;
-    for (int row = r0; row < r1 && ok; ++row) {
-      const int2 b = row_band(row);
-      for (int k0 = b.x; k0 < b.y; k0 += chunk, ++u) {
-        const int st = u % kGvStages;
-        if (!ptx::mbar_wait(&full[st], (u / kGvStages) & 1, &abort_flag)) {
+    for (int i = 0; i < nseg; ++i) {
+      const GvSeg g = seg_at(i);
+      if (g.stage != cur) {
+        if (cur >= 0) {
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&empty[cur % kGvStages]);
+        }
+        cur = g.stage;
+        // warp-uniform: no lane runs on into the next stage or a __syncwarp alone
+        ok = __all_sync(0xffffffffu, ptx::mbar_wait(&full[cur % kGvStages], (cur / kGvStages) & 1, &abort_flag));
+        if (!ok) {
           if (lane == 0) {
             atomicExch(&abort_flag, 1u);
             atomicOr(status, kStatusTimeout);
           }
-          ok = false;
           break;
         }
-        const int len = min(chunk, b.y - k0), slice = len / kGvConsumers;  // a multiple of 4 floats
-        const float4* buf = reinterpret_cast<const float4*>(sbuf + (size_t)st * chunk + warp * slice);
-        const float4* w4 = reinterpret_cast<const float4*>(W + k0 + warp * slice);
+      }
+      // rows are dealt to the warps in turn: a warp sums whole rows (all
+      // segments of a row go to the same warp), and the rows of different
+      // warps stream in parallel
+      if (g.row % kGvConsumers != warp) continue;
+      const float4* buf = reinterpret_cast<const float4*>(sbuf + (size_t)(cur % kGvStages) * chunk + g.off);
+      const float4* w4 = reinterpret_cast<const float4*>(W + g.k0);
+      const int n4 = g.len / 4;
+      for (int q0 = 0; q0 < n4; q0 += 8 * 32) {  // FP32 partials over at most 8 float4 a lane
+        const int qe = min(n4, q0 + 8 * 32);
         float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
-        for (int q = lane; q < slice / 4; q += 32) {
+#pragma unroll 4
+        for (int q = q0 + lane; q < qe; q += 32) {
           const float4 r = buf[q];
           const float4 w = __ldg(w4 + q);
           ax = fmaf(r.x, w.x, ax);
@@ -148,15 +204,17 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
           az = fmaf(r.z, w.z, az);
           aw = fmaf(r.w, w.w, aw);
         }
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&empty[st]);
         lacc = df_add(lacc, (ax + ay) + (az + aw));
       }
-      if (!ok) break;
-      SRW_CHECK(status, row - r0 < rows_per_block);
-      const dfloat v = df_warp_sum(lacc);  // the row's sum (every row has at least one chunk)
-      if (lane == 0) spart[(row - r0) * kGvConsumers + warp] = make_float2(v.hi, v.lo);
-      lacc = {0.f, 0.f};
+      if (g.done) {  // each lane leaves its share of the row; the epilogue adds the 32
+        SRW_CHECK(status, g.row < rows_per_block);
+        spart[(size_t)lane * ps + g.row] = make_float2(lacc.hi, lacc.lo);
+        lacc = {0.f, 0.f};
+      }
+    }
+    if (ok && cur >= 0) {
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[cur % kGvStages]);
     }
   }
   __syncthreads();
@@ -167,9 +225,9 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   if (abort_flag == 0u) {
     for (int rl = threadIdx.x; rl < nrows; rl += kGvThreads) {
       const int j = r0 + rl;
-      dfloat ms = {0.f, 0.f};
-      for (int w = 0; w < kGvConsumers; ++w) {
-        const float2 v = spart[rl * kGvConsumers + w];
+      dfloat ms = {0.f, 0.f};  // the row's sum: the 32 lane shares of its warp
+      for (int l = 0; l < 32; ++l) {
+        const float2 v = spart[(size_t)l * ps + rl];
         ms = df_add(ms, dfloat{v.x, v.y});
       }
       // delta mode: W holds W(theta) - W_ref, and the FP64 reference fold is added back
@@ -295,16 +353,24 @@ int fold_point_grid(const srw_ctx* h) {
 
 static size_t gv_smem(const srw_ctx* h) {
   const int chunk = h->ld_r < kGvChunk ? h->ld_r : kGvChunk;
-  return sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * (size_t)kGvConsumers * gv_rows_per_block(h);
+  return sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * 32 * (size_t)gv_part_stride(gv_rows_per_block(h)) +
+         sizeof(int4) * (size_t)(h->gv_blocks > 0 ? h->gv_max_segs : 0);
 }
 
 // Per row of R its nonzero band [lo, hi): lo the first nonzero column rounded
-// down to 4 floats (16-byte copies), the length rounded up to 32 floats (eight
-// consumer warps x float4) and kept inside the padded row; an all-zero row
-// keeps 32 columns.  Then the rows are split over the fold_point_grid blocks
-// so that each streams about the same number of bytes (plus a per-row cost).
+// down to 4 floats (16-byte copies), the length rounded up to 32 floats and
+// kept inside the padded row; an all-zero row keeps 32 columns.  The rows are
+// split over the fold_point_grid blocks so that each takes about the same
+// time to stream: a row costs its band plus kGvRowCost floats, the fixed cost
+// of the bulk copy that brings it in (measured on GB300: a copy takes about
+// 0.16 us plus 0.04 us per KB, one after another on an SM, so a block of many
+// short rows is bound by its number of copies); each block's bands are cut
+// into its stream segments: consecutive bands packed into stages of up to
+// kGvChunk floats, a band that does not fit in the rest of a started stage
+// opening the next one, a band longer than a stage cut into stage-sized
+// pieces.
 cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R) {
-  const int n_rec = h->n_rec, ld = h->ld_r;
+  const int n_rec = h->n_rec, ld = h->ld_r, chunk = ld < kGvChunk ? ld : kGvChunk;
   std::vector<int2> band(n_rec);
   long long total = 0;
   for (int r = 0; r < n_rec; ++r) {
@@ -320,7 +386,7 @@ cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R) {
     if (len > ld) len = ld;
     if (lo + len > ld) lo = ld - len;
     band[r] = make_int2(lo, lo + len);
-    total += len + 64;  // + a per-row cost (the row's reduction and epilogue)
+    total += len + kGvRowCost;
   }
   const int nb = fold_point_grid(h);
   std::vector<int> start(nb + 1, n_rec);
@@ -328,21 +394,55 @@ cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R) {
   long long acc = 0;
   int b = 1, max_rows = 0;
   for (int r = 0; r < n_rec && b < nb; ++r) {
-    acc += band[r].y - band[r].x + 64;
+    acc += band[r].y - band[r].x + kGvRowCost;
     if (acc * nb >= total * b) start[b++] = r + 1;
   }
   for (int k = 0; k < nb; ++k) max_rows = std::max(max_rows, start[k + 1] - start[k]);
+  // segments {row | done << 30, k0, len, off | stage << 16}, block by block
+  std::vector<int4> seg;
+  std::vector<int> seg_start(nb + 1, 0);
+  int max_segs = 0;
+  for (int k = 0; k < nb; ++k) {
+    seg_start[k] = (int)seg.size();
+    int stage = 0, fill = 0;
+    for (int r = start[k]; r < start[k + 1]; ++r) {
+      int k0 = band[r].x;
+      while (k0 < band[r].y) {
+        const int rem = band[r].y - k0;
+        if (fill > 0 && rem > chunk - fill) {  // does not fit: next stage
+          ++stage;
+          fill = 0;
+        }
+        const int len = std::min(rem, chunk - fill);
+        const int done = len == rem ? 1 : 0;
+        if (stage >= 32768) return cudaErrorInvalidValue;
+        seg.push_back(make_int4((r - start[k]) | (done << 30), k0, len, fill | (stage << 16)));
+        fill += len;
+        k0 += len;
+        if (fill == chunk) {
+          ++stage;
+          fill = 0;
+        }
+      }
+    }
+    max_segs = std::max(max_segs, (int)seg.size() - seg_start[k]);
+  }
+  seg_start[nb] = (int)seg.size();
   cudaError_t e = cudaSuccess;
-  if (!h->d_gv_band && (e = dev_malloc(&h->d_gv_band, sizeof(int2) * (size_t)n_rec)) != cudaSuccess) return e;
+  if (!h->d_gv_seg && (e = dev_malloc(&h->d_gv_seg, sizeof(int4) * seg.size())) != cudaSuccess) return e;
+  if (!h->d_gv_segs && (e = dev_malloc(&h->d_gv_segs, sizeof(int) * (size_t)(nb + 1))) != cudaSuccess) return e;
   if (!h->d_gv_rows && (e = dev_malloc(&h->d_gv_rows, sizeof(int) * (size_t)(nb + 1))) != cudaSuccess) return e;
-  h->device_bytes += sizeof(int2) * (size_t)n_rec + sizeof(int) * (size_t)(nb + 1);
-  if ((e = cudaMemcpy(h->d_gv_band, band.data(), sizeof(int2) * (size_t)n_rec, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  h->device_bytes += sizeof(int4) * seg.size() + 2 * sizeof(int) * (size_t)(nb + 1);
+  if ((e = cudaMemcpy(h->d_gv_seg, seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_gv_segs, seg_start.data(), sizeof(int) * (size_t)(nb + 1), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
       (e = cudaMemcpy(h->d_gv_rows, start.data(), sizeof(int) * (size_t)(nb + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
   long long bytes = 0;
   for (const int2& x : band) bytes += 4LL * (x.y - x.x);
   h->gv_blocks = nb;
   h->gv_max_rows = max_rows;
+  h->gv_max_segs = max_segs;
   h->gv_bytes = bytes;
   return cudaSuccess;
 }
@@ -358,8 +458,8 @@ cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out
   const double* muref = delta ? h->d_muref64 : nullptr;
   fold_point_kernel<<<fold_point_grid(h), kGvThreads, smem, s>>>(
       h->d_R, h->n_rec, h->ld_r, gv_rows_per_block(h), W, muref, h->d_n64, h->d_b64, h->d_mask, h->d_cdata, musig_out,
-      mu_out, h->d_part, h->d_ticket, out, h->d_status, inject_timeout(), h->d_gv_band,
-      h->gv_blocks > 0 ? h->d_gv_rows : nullptr);
+      mu_out, h->d_part, h->d_ticket, out, h->d_status, inject_timeout(), h->gv_blocks > 0 ? h->d_gv_seg : nullptr,
+      h->gv_blocks > 0 ? h->d_gv_segs : nullptr, h->gv_blocks > 0 ? h->d_gv_rows : nullptr);
   return launch_result();
 }
 
@@ -382,7 +482,8 @@ cudaError_t launch_fold_point_after(const srw_ctx* h, const float* W, double* ou
                                            (const double*)h->d_b64, (const unsigned char*)h->d_mask,
                                            (const double*)h->d_cdata, (float*)nullptr, (float*)nullptr, h->d_part,
                                            h->d_ticket, out, h->d_status, inject_timeout(),
-                                           (const int2*)h->d_gv_band,
+                                           (const int4*)(h->gv_blocks > 0 ? h->d_gv_seg : nullptr),
+                                           (const int*)(h->gv_blocks > 0 ? h->d_gv_segs : nullptr),
                                            (const int*)(h->gv_blocks > 0 ? h->d_gv_rows : nullptr));
   return e != cudaSuccess ? e : launch_result();
 }
@@ -506,7 +607,7 @@ extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld
   const int grid = (n_rec + rpb - 1) / rpb;
   if (grid > kNoAllocMaxBlocks) return bad("too many blocks for the scratch array");
   const int chunk = ld < kGvChunk ? ld : kGvChunk;
-  const size_t smem = sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * (size_t)kGvConsumers * rpb;
+  const size_t smem = sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * 32 * (size_t)gv_part_stride(rpb);
   if (smem > 200 * 1024) return bad("n_rec too large for the fold's shared memory");
   cudaStream_t s = (cudaStream_t)stream;
   NoAllocScratch* sc = nd.scratch;
@@ -518,7 +619,7 @@ extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld
   cdata_kernel<<<1, 1024, 0, s>>>(counts, mask, n_rec, &sc->c_data);
   fold_point_kernel<<<grid, kGvThreads, smem, s>>>(R, n_rec, ld, rpb, W, nullptr, counts, bkg, mask, &sc->c_data,
                                                     nullptr, nullptr, sc->parts, &sc->ticket, out, &sc->status,
-                                                    inject_timeout(), nullptr, nullptr);
+                                                    inject_timeout(), nullptr, nullptr, nullptr);
   if ((e = launch_result()) != cudaSuccess) {
     g_noalloc_err = cudaGetErrorString(e);
     return SRW_ECUDA;

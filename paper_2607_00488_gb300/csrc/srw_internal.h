@@ -202,9 +202,10 @@ struct srw_ctx {
   int part_cap = 0;
   unsigned* d_ticket = nullptr;
   unsigned* d_status = nullptr;
-  int2* d_gv_band = nullptr;   // [n_rec] single-point GEMV: nonzero band {lo, hi} of each row of R
+  int4* d_gv_seg = nullptr;    // single-point GEMV: stream segments of every block (rows' nonzero bands)
+  int* d_gv_segs = nullptr;    // [gv_blocks + 1] first segment of each GEMV block
   int* d_gv_rows = nullptr;    // [gv_blocks + 1] first row of each GEMV block (band-balanced split)
-  int gv_blocks = 0, gv_max_rows = 0;
+  int gv_blocks = 0, gv_max_rows = 0, gv_max_segs = 0;
   long long gv_bytes = 0;      // bytes of R the GEMV streams (the bands)
   double* d_bpart = nullptr;   // batched partials [n_tiles][P]
   size_t bpart_cap = 0;
