@@ -21,6 +21,9 @@
 // 1.7e-4 at a point 220 units from the data (FP32 emulation and GB300 agree),
 // 16-term chains by 2e-5.
 
+#include <algorithm>
+#include <vector>
+
 #include "dfloat.cuh"
 #include "poisson.cuh"
 #include "srw_internal.h"
@@ -34,7 +37,6 @@ constexpr int BK = 16;
 constexpr int THR = 256;  // 16 x 16 threads
 constexpr int TM = 4;     // points per thread
 constexpr int TN = 8;     // rec bins per thread
-constexpr int CHUNK = 1;  // K tiles per compensated chunk
 
 // Coupling monomials c_b(theta) (see srw_internal.h) in double-float
 // arithmetic, returned as hi + lo float pairs so that W carries no per-theta
@@ -53,15 +55,15 @@ __device__ __forceinline__ void coefficients(const float* th, dfloat s, const Co
   }
 }
 
-__global__ void __launch_bounds__(THR)
+__global__ void __launch_bounds__(THR, 2)
 fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef cref, const float* __restrict__ shat,
                  const float* __restrict__ shat_lo, int k_pad, const float* __restrict__ R, int n_rec, int ld,
                  const double* __restrict__ n64, const double* __restrict__ b64,
                  const unsigned char* __restrict__ mask, double* __restrict__ parts,
-                 float* __restrict__ musig_out, unsigned* __restrict__ status) {
+                 float* __restrict__ musig_out, unsigned* __restrict__ status, const int2* __restrict__ krange) {
   __shared__ float cs[BM][2 * kNB + 1];
-  __shared__ __align__(16) float Ws[BK][BM];
-  __shared__ __align__(16) float Rs[BK][BN + 4];
+  __shared__ __align__(16) float Ws[2][BK][BM];
+  __shared__ __align__(16) float Rs[2][BK][BN + 4];
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
@@ -88,50 +90,66 @@ fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef c
 #pragma unroll
     for (int c = 0; c < TN; ++c) acc[r][c] = sum[r][c] = comp[r][c] = 0.f;
 
-  const int n_kt = k_pad / BK;
-  for (int kt = 0; kt < n_kt; ++kt) {
+  // K tiles of this rec tile that hold nonzero response; outside them every
+  // product is an exact zero
+  const int2 kr = krange ? krange[blockIdx.y] : make_int2(0, k_pad / BK);
+  // register staging of the next tile: two float4 of R, the shat values of
+  // one k (hi, lo) for this thread's W elements
+  const int wk = tid & (BK - 1), mg = (tid >> 4) * TM;
+  float4 rv[2];
+  float sh[kNB], sl[kNB];
+  auto load_tile = [&](int kt) {
     const int k0 = kt * BK;
-    __syncthreads();
-    {  // produce W^T tile: W[p][k] = sum_b c_b(p) shat_b[k]
-      const int k = tid & (BK - 1), mg = (tid >> 4) * TM;
-      float sh[kNB], sl[kNB];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int f = tid + rr * THR, row = f >> 2, c4 = f & 3, j = j0 + row;
+      SRW_CHECK(status, k0 + c4 * 4 + 4 <= ld);
+      rv[rr] = j < n_rec ? __ldg(reinterpret_cast<const float4*>(R + (size_t)j * ld + k0 + c4 * 4))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int b = 0; b < kNB; ++b) {
+      sh[b] = __ldg(shat + (size_t)b * k_pad + k0 + wk);
+      sl[b] = __ldg(shat_lo + (size_t)b * k_pad + k0 + wk);
+    }
+  };
+  auto store_tile = [&](int buf) {
+    // W^T tile: W[p][k] = sum_b c_b(p) shat_b[k], (c_hi + c_lo)(s_hi + s_lo) without lo*lo
+    float v[TM];
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+      float s = 0.f, t = 0.f;
 #pragma unroll
       for (int b = 0; b < kNB; ++b) {
-        sh[b] = __ldg(shat + (size_t)b * k_pad + k0 + k);
-        sl[b] = __ldg(shat_lo + (size_t)b * k_pad + k0 + k);
+        s = fmaf(cs[mg + r][b], sh[b], s);
+        t = fmaf(cs[mg + r][kNB + b], sh[b], fmaf(cs[mg + r][b], sl[b], t));
       }
-      float v[TM];
-#pragma unroll
-      for (int r = 0; r < TM; ++r) {
-        // (c_hi + c_lo)(s_hi + s_lo) without the lo*lo term
-        float s = 0.f, t = 0.f;
-#pragma unroll
-        for (int b = 0; b < kNB; ++b) {
-          s = fmaf(cs[mg + r][b], sh[b], s);
-          t = fmaf(cs[mg + r][kNB + b], sh[b], fmaf(cs[mg + r][b], sl[b], t));
-        }
-        v[r] = s + t;
-      }
-      *reinterpret_cast<float4*>(&Ws[k][mg]) = make_float4(v[0], v[1], v[2], v[3]);
+      v[r] = s + t;
     }
+    *reinterpret_cast<float4*>(&Ws[buf][wk][mg]) = make_float4(v[0], v[1], v[2], v[3]);
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {  // R tile, transposed into Rs[k][j]
       const int f = tid + rr * THR, row = f >> 2, c4 = f & 3;
-      const int j = j0 + row;
-      SRW_CHECK(status, k0 + c4 * 4 + 4 <= ld);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < n_rec) v = __ldg(reinterpret_cast<const float4*>(R + (size_t)j * ld + k0 + c4 * 4));
-      Rs[c4 * 4 + 0][row] = v.x;
-      Rs[c4 * 4 + 1][row] = v.y;
-      Rs[c4 * 4 + 2][row] = v.z;
-      Rs[c4 * 4 + 3][row] = v.w;
+      Rs[buf][c4 * 4 + 0][row] = rv[rr].x;
+      Rs[buf][c4 * 4 + 1][row] = rv[rr].y;
+      Rs[buf][c4 * 4 + 2][row] = rv[rr].z;
+      Rs[buf][c4 * 4 + 3][row] = rv[rr].w;
     }
+  };
+
+  __syncthreads();  // the block's coefficients are in shared memory
+  if (kr.x < kr.y) load_tile(kr.x);
+  for (int kt = kr.x; kt < kr.y; ++kt) {
+    const int buf = (kt - kr.x) & 1;
+    // the other buffer was last read before the previous iteration's barrier
+    store_tile(buf);
     __syncthreads();
+    if (kt + 1 < kr.y) load_tile(kt + 1);  // in flight during the FMAs below
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      const float4 a = *reinterpret_cast<const float4*>(&Ws[k][ty * TM]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Rs[k][tx * TN]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Rs[k][tx * TN + 4]);
+      const float4 a = *reinterpret_cast<const float4*>(&Ws[buf][k][ty * TM]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Rs[buf][k][tx * TN]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Rs[buf][k][tx * TN + 4]);
       const float av[TM] = {a.x, a.y, a.z, a.w};
       const float bv[TN] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -139,18 +157,17 @@ fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef c
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
-    if ((kt + 1) % CHUNK == 0 || kt + 1 == n_kt) {
+    // each 16-term chain is added to the running sum with Kahan compensation
 #pragma unroll
-      for (int r = 0; r < TM; ++r)
+    for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int c = 0; c < TN; ++c) {
-          const float y = acc[r][c] - comp[r][c];
-          const float t = sum[r][c] + y;
-          comp[r][c] = (t - sum[r][c]) - y;
-          sum[r][c] = t;
-          acc[r][c] = 0.f;
-        }
-    }
+      for (int c = 0; c < TN; ++c) {
+        const float y = acc[r][c] - comp[r][c];
+        const float t = sum[r][c] + y;
+        comp[r][c] = (t - sum[r][c]) - y;
+        sum[r][c] = t;
+        acc[r][c] = 0.f;
+      }
   }
 
   if (musig_out != nullptr) {  // batched folded spectra
@@ -198,9 +215,39 @@ cudaError_t launch_fold_simt(const srw_ctx* h, const float* theta, int P, double
                              int* n_parts, float* musig_out) {
   const dim3 grid((P + BM - 1) / BM, (h->n_rec + BN - 1) / BN);
   fold_simt_kernel<<<grid, THR, 0, s>>>(theta, P, df_from_double(h->sin2w), h->cref, h->d_shat, h->d_shat_lo, h->k_pad, h->d_R, h->n_rec,
-                                        h->ld_r, h->d_n64, h->d_bref64, h->d_mask, parts, musig_out, h->d_status);
+                                        h->ld_r, h->d_n64, h->d_bref64, h->d_mask, parts, musig_out, h->d_status,
+                                        h->d_simt_kr);
   if (n_parts) *n_parts = (int)grid.y;
   return launch_result();
+}
+
+// Per rec tile of BN bins the K tiles [first, end) between its first and last
+// nonzero column of R (FP32, exact zeros outside; a tile without any nonzero
+// element gets an empty range).
+cudaError_t simt_prepare(srw_ctx* h, const std::vector<float>& R) {
+  const int nt = fold_simt_parts(h->n_rec), n_kt = h->k_pad / BK, cols = std::min(h->ld_r, h->k_pad);
+  std::vector<int2> kr(nt);
+  for (int t = 0; t < nt; ++t) {
+    int first = cols, last = -1;
+    for (int j = t * BN; j < std::min(h->n_rec, (t + 1) * BN); ++j) {
+      const float* row = R.data() + (size_t)j * h->ld_r;
+      for (int k = 0; k < first; ++k)
+        if (row[k] != 0.f) {
+          first = k;
+          break;
+        }
+      for (int k = cols - 1; k > last; --k)
+        if (row[k] != 0.f) {
+          last = k;
+          break;
+        }
+    }
+    kr[t] = last < 0 ? make_int2(0, 0) : make_int2(first / BK, std::min(n_kt, last / BK + 1));
+  }
+  cudaError_t e = cudaSuccess;
+  if (!h->d_simt_kr && (e = dev_malloc(&h->d_simt_kr, sizeof(int2) * (size_t)nt)) != cudaSuccess) return e;
+  h->device_bytes += sizeof(int2) * (size_t)nt;
+  return cudaMemcpy(h->d_simt_kr, kr.data(), sizeof(int2) * (size_t)nt, cudaMemcpyHostToDevice);
 }
 
 }  // namespace srw

@@ -139,7 +139,7 @@ static void release(srw_ctx* h) {
   dfree(h->d_ssm32); dfree(h->d_esm32); dfree(h->d_shat); dfree(h->d_R); dfree(h->d_rhi); dfree(h->d_rlo); dfree(h->d_rhi16); dfree(h->d_rlo16); dfree(h->d_rinv); dfree(h->d_coef); dfree(h->d_linM); dfree(h->d_lin); dfree(h->d_linp);
   dfree(h->d_n64); dfree(h->d_b64); dfree(h->d_muref64); dfree(h->d_bref64); dfree(h->d_nbm); dfree(h->d_nb2); dfree(h->d_nb4); dfree(h->d_mask); dfree(h->d_cdata);
   dfree(h->d_W); dfree(h->d_S); dfree(h->d_musig); dfree(h->d_mu); dfree(h->d_part); dfree(h->d_ticket);
-  dfree(h->d_status); dfree(h->d_gv_seg); dfree(h->d_gv_segs); dfree(h->d_gv_rows); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
+  dfree(h->d_status); dfree(h->d_gv_seg); dfree(h->d_simt_kr); dfree(h->d_gv_segs); dfree(h->d_gv_rows); dfree(h->d_bpart); dfree(h->d_theta); dfree(h->d_out); dfree(h->d_theta0);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   h->own_stream = nullptr;
   for (auto& ev : h->ev_fold)
@@ -738,6 +738,7 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
   std::vector<float> Rh((size_t)n_rec * h->ld_r);
   CREATE_CUDA(cudaMemcpy(Rh.data(), h->d_R, sizeof(float) * Rh.size(), cudaMemcpyDeviceToHost), "read R");
   CREATE_CUDA(gemv_prepare(h, Rh), "GEMV bands");
+  CREATE_CUDA(simt_prepare(h, Rh), "FP32 fold K ranges");
   // ---- tensor-core path: BF16 hi/lo split of R and TMA descriptors
   if (tc_supported(h)) {
     CREATE_CUDA(dalloc(h, &h->d_rhi, (size_t)h->rec_pad * h->k_pad), "alloc R hi");

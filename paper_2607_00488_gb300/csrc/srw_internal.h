@@ -205,6 +205,7 @@ struct srw_ctx {
   int4* d_gv_seg = nullptr;    // single-point GEMV: stream segments of every block (rows' nonzero bands)
   int* d_gv_segs = nullptr;    // [gv_blocks + 1] first segment of each GEMV block
   int* d_gv_rows = nullptr;    // [gv_blocks + 1] first row of each GEMV block (band-balanced split)
+  int2* d_simt_kr = nullptr;   // FP32 batched fold: K-tile range [first, end) of each 128-bin rec tile
   int gv_blocks = 0, gv_max_rows = 0, gv_max_segs = 0;
   long long gv_bytes = 0;      // bytes of R the GEMV streams (the bands)
   double* d_bpart = nullptr;   // batched partials [n_tiles][P]
@@ -300,6 +301,7 @@ int fold_point_grid(const srw_ctx* h);
 // Nonzero bands of R's rows and the band-balanced row split of the GEMV
 // (R: the device R copied to the host, n_rec x ld_r).
 cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R);
+cudaError_t simt_prepare(srw_ctx* h, const std::vector<float>& R);
 void fold_point_init();
 int fold_simt_parts(int n_rec);
 cudaError_t launch_fold_point(const srw_ctx* h, const float* W, float* musig_out, float* mu_out, double* out,
