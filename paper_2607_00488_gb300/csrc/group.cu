@@ -394,8 +394,7 @@ srw_status srw_group_loglik(srw_group g, const float* theta, double* out, int wh
   const float* th = theta;
   double* o = out;
   if (where == SRW_HOST) {
-    for (size_t q = 0; q < (size_t)g->P_total * 5; ++q)
-      if (!std::isfinite(theta[q])) return gfail(g, SRW_EINVAL, "theta must be finite");
+    if (!srw::all_finite(theta, (size_t)g->P_total * 5)) return gfail(g, SRW_EINVAL, "theta must be finite");
     // a host-pointer call reports the device status of this call only
     G_CUDA(g, cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), s), "status reset");
     G_CUDA(g, cudaMemcpyAsync(g->d_theta, theta, sizeof(float) * 5 * (size_t)g->P_total, cudaMemcpyHostToDevice, s),

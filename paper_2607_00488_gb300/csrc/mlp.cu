@@ -1258,8 +1258,7 @@ static srw_status fit_impl(srw_surrogate s, const float* theta, long long n, con
   if (o->batch < srw::kBM || o->batch % srw::kBM || o->epochs < 0 || !(o->lr > 0.f) || !(o->lr_final >= 0.f))
     return sfail(s, SRW_EINVAL, "batch must be a positive multiple of 128; epochs >= 0; lr > 0");
   if (o->precision < SRW_FP32 || o->precision > SRW_FP16X3) return sfail(s, SRW_EINVAL, "bad precision");
-  for (long long q = 0; q < n * 5; ++q)
-    if (!std::isfinite(theta[q])) return sfail(s, SRW_EINVAL, "theta must be finite");
+  if (!srw::all_finite(theta, (size_t)(n * 5))) return sfail(s, SRW_EINVAL, "theta must be finite");
   srw_ctx* h = s->h;
   cudaStream_t st = s->stream;
   const int M = o->batch, NO = s->n_out_pad, NR = s->n_out;
@@ -1368,8 +1367,7 @@ srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, doub
     if (r == SRW_OK && !stream) S_CUDA(s, cudaStreamSynchronize(st), "sync");
     return r;
   }
-  for (long long q = 0; q < (long long)P * 5; ++q)
-    if (!std::isfinite(theta[q])) return sfail(s, SRW_EINVAL, "theta must be finite");
+  if (!srw::all_finite(theta, (size_t)((long long)P * 5))) return sfail(s, SRW_EINVAL, "theta must be finite");
   float* d_th = nullptr;
   double* d_out = nullptr;
   S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, st), "alloc");

@@ -920,8 +920,7 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   const float* th = theta;
   double* o = out;
   if (where == SRW_HOST) {
-    for (size_t q = 0; q < (size_t)P * 5; ++q)
-      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    if (!all_finite(theta, (size_t)P * 5)) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
     // a host-pointer call reports the device status of this call only
@@ -1027,8 +1026,7 @@ srw_status srw_loglik_linear(srw_handle h, const float* theta, int P, double* ou
   const float* th = theta;
   double *o = out, *g = grad, *d_g = nullptr;
   if (where == SRW_HOST) {
-    for (size_t q = 0; q < (size_t)P * 5; ++q)
-      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    if (!all_finite(theta, (size_t)P * 5)) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
     // a host-pointer call reports the device status of this call only
@@ -1075,8 +1073,7 @@ srw_status srw_loglik_profiled(srw_handle h, const float* theta, int P, double s
   const float* th = theta;
   double *o = out, *a = alpha, *d_a = nullptr;
   if (where == SRW_HOST) {
-    for (size_t q = 0; q < (size_t)P * 5; ++q)
-      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    if (!all_finite(theta, (size_t)P * 5)) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
     // a host-pointer call reports the device status of this call only
@@ -1128,8 +1125,7 @@ srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* ou
     if (st != SRW_OK) return st;
   }
   if (where == SRW_HOST) {
-    for (size_t q = 0; q < (size_t)P * 5; ++q)
-      if (!std::isfinite(theta[q])) return fail(h, SRW_EINVAL, "theta must be finite");
+    if (!all_finite(theta, (size_t)P * 5)) return fail(h, SRW_EINVAL, "theta must be finite");
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
     // a host-pointer call reports the device status of this call only

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <cstring>
 #include <vector>
 
 #include "../../include/srw.h"
@@ -300,6 +301,19 @@ cudaError_t launch_add_ref(const srw_ctx* h, float* out, int P, cudaStream_t s);
 int fold_point_grid(const srw_ctx* h);
 // Nonzero bands of R's rows and the band-balanced row split of the GEMV
 // (R: the device R copied to the host, n_rec x ld_r).
+// True when every one of the n floats is finite (exponent field not all ones):
+// one branch-free pass over their bits, which the host compiler vectorises
+// (a per-element isfinite with an early exit does not).
+inline bool all_finite(const float* x, size_t n) {
+  uint32_t bad = 0u;
+  for (size_t q = 0; q < n; ++q) {
+    uint32_t b;
+    std::memcpy(&b, x + q, sizeof b);
+    bad |= (uint32_t)((b & 0x7f800000u) == 0x7f800000u);
+  }
+  return bad == 0u;
+}
+
 cudaError_t gemv_prepare(srw_ctx* h, const std::vector<float>& R);
 cudaError_t simt_prepare(srw_ctx* h, const std::vector<float>& R);
 void fold_point_init();
