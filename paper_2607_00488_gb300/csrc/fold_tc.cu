@@ -178,6 +178,7 @@ __device__ __forceinline__ int kb_at(int2 kr, int kk) {
 }
 
 constexpr int kMaxGroups = 4096;  // configurations of one grouped launch
+constexpr int kPrefetch = 2;      // R blocks prefetched into L2 this many stages ahead
 
 // K-block walk of the rec tile at n0.  (Staging the walks, or the epilogue's
 // per-bin constants, in shared memory was measured: no gain, and 4.8 % slower
@@ -518,6 +519,14 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           ptx::mbar_arrive_expect_tx(&r_full[st], bytes);
           tma_load_2d(b_hi(st), mh, kb * BK, n0, &r_full[st]);
           if (X3) tma_load_2d(b_lo(st), ml, kb * BK, n0, &r_full[st]);
+          // warm L2 with the block kPrefetch stages ahead: with a two-stage ring
+          // a response that does not stay in L2 (many configurations) would
+          // otherwise expose the HBM latency at every stage
+          if (kk + kPrefetch < kb_count<BK>(kr)) {
+            const int kbp = kb_at<BK>(kr, kk + kPrefetch);
+            tma_prefetch_2d(mh, kbp * BK, n0);
+            if (X3) tma_prefetch_2d(ml, kbp * BK, n0);
+          }
           issued_g = g + 1;
         }
       }

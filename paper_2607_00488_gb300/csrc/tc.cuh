@@ -1,6 +1,6 @@
 // tcgen05 / TMA helpers for sm_103a (inline PTX): tensor-memory allocation,
 // kind::f16 MMAs with FP32 accumulation, commits to mbarriers, TMEM loads,
-// 2-D tiled TMA loads, shared-memory matrix descriptors for 128-byte-swizzled
+// 2-D tiled TMA loads and L2 prefetches, shared-memory matrix descriptors for 128-byte-swizzled
 // K-major operands, and warp-uniform bounded waits.
 #pragma once
 
@@ -62,6 +62,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
           ptx::smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_addr(bar))
       : "memory");
+}
+
+// Hint: bring the tile at {x, y} of `map` into L2 (no shared memory, no
+// completion); same coordinate rules as tma_load_2d.
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
