@@ -179,6 +179,7 @@ __device__ __forceinline__ int kb_at(int2 kr, int kk) {
 
 constexpr int kMaxGroups = 4096;  // configurations of one grouped launch
 constexpr int kPrefetch = 2;      // R blocks prefetched into L2 this many stages ahead
+constexpr double kL2ResidentBytes = 64.0 * 1024 * 1024;  // responses up to this size stay in L2 (129 MB)
 
 // K-block walk of the rec tile at n0.  (Staging the walks, or the epilogue's
 // per-bin constants, in shared memory was measured: no gain, and 4.8 % slower
@@ -205,6 +206,7 @@ struct TcLaunch {
   float* musig_out;            // single configuration only: [P][n_rec] folded deviations
   unsigned* status;
   int inject;                  // injected timeout (host-side fault injection): CTA 0's epilogue gives up
+  int prefetch;                // 1: prefetch R blocks into L2 ahead of the ring (responses that L2 does not hold)
 };
 
 // Item loops: a grid stride written directly in blockIdx / gridDim / a kernel
@@ -520,9 +522,9 @@ fold_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           tma_load_2d(b_hi(st), mh, kb * BK, n0, &r_full[st]);
           if (X3) tma_load_2d(b_lo(st), ml, kb * BK, n0, &r_full[st]);
           // warm L2 with the block kPrefetch stages ahead: with a two-stage ring
-          // a response that does not stay in L2 (many configurations) would
-          // otherwise expose the HBM latency at every stage
-          if (kk + kPrefetch < kb_count<BK>(kr)) {
+          // a response that does not stay in L2 (many configurations, or one
+          // large one) would otherwise expose the HBM latency at every stage
+          if (L.prefetch && kk + kPrefetch < kb_count<BK>(kr)) {
             const int kbp = kb_at<BK>(kr, kk + kPrefetch);
             tma_prefetch_2d(mh, kbp * BK, n0);
             if (X3) tma_prefetch_2d(ml, kbp * BK, n0);
@@ -1011,6 +1013,8 @@ cudaError_t launch_fold_tc(const srw_ctx* h, const float* theta, int P, int prec
   L.musig_out = musig_out;
   L.status = h->d_status;
   L.inject = inject_timeout();
+  // a response whose splits fill more than about half of L2 is streamed from HBM
+  L.prefetch = (double)h->rec_pad * h->k_pad * 2.0 * 2.0 > kL2ResidentBytes ? 1 : 0;
   if (n_parts) *n_parts = L.g0.n_tiles;
   if (h->d_coef == nullptr || h->coef_cap < P) return cudaErrorInvalidValue;
   coef_kernel<<<(P + 255) / 256, 256, 0, s>>>(L.g0, theta, f16 ? 1 : 0, h->d_coef);
@@ -1045,6 +1049,7 @@ cudaError_t launch_fold_tc_group(int bn_max, int precision, const TcGroup* d_gro
   L.musig_out = nullptr;
   L.status = status;
   L.inject = inject_timeout();
+  L.prefetch = 1;  // the configurations' responses together rarely stay in L2
   static const CUtensorMap unused{};  // grouped launches read each configuration's maps from its descriptor
   return launch_grouped(bn_max == 256 ? 256 : 128, precision, unused, unused, L, n_cta, s);
 }
