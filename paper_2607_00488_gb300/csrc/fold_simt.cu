@@ -93,11 +93,11 @@ fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef c
   // K tiles of this rec tile that hold nonzero response; outside them every
   // product is an exact zero
   const int2 kr = krange ? krange[blockIdx.y] : make_int2(0, k_pad / BK);
-  // register staging of the next tile: two float4 of R, the shat values of
-  // one k (hi, lo) for this thread's W elements
+  // register staging of the next tile's R (two float4 a thread); the shat
+  // values are loaded when the tile's W is formed (kept live across the FMA
+  // loop they spilled registers at two blocks per SM)
   const int wk = tid & (BK - 1), mg = (tid >> 4) * TM;
   float4 rv[2];
-  float sh[kNB], sl[kNB];
   auto load_tile = [&](int kt) {
     const int k0 = kt * BK;
 #pragma unroll
@@ -107,14 +107,15 @@ fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef c
       rv[rr] = j < n_rec ? __ldg(reinterpret_cast<const float4*>(R + (size_t)j * ld + k0 + c4 * 4))
                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  };
+  auto store_tile = [&](int buf, int kt) {
+    // W^T tile: W[p][k] = sum_b c_b(p) shat_b[k], (c_hi + c_lo)(s_hi + s_lo) without lo*lo
+    float sh[kNB], sl[kNB];
 #pragma unroll
     for (int b = 0; b < kNB; ++b) {
-      sh[b] = __ldg(shat + (size_t)b * k_pad + k0 + wk);
-      sl[b] = __ldg(shat_lo + (size_t)b * k_pad + k0 + wk);
+      sh[b] = __ldg(shat + (size_t)b * k_pad + kt * BK + wk);
+      sl[b] = __ldg(shat_lo + (size_t)b * k_pad + kt * BK + wk);
     }
-  };
-  auto store_tile = [&](int buf) {
-    // W^T tile: W[p][k] = sum_b c_b(p) shat_b[k], (c_hi + c_lo)(s_hi + s_lo) without lo*lo
     float v[TM];
 #pragma unroll
     for (int r = 0; r < TM; ++r) {
@@ -142,7 +143,7 @@ fold_simt_kernel(const float* __restrict__ theta, int P, dfloat sin2w, CoefRef c
   for (int kt = kr.x; kt < kr.y; ++kt) {
     const int buf = (kt - kr.x) & 1;
     // the other buffer was last read before the previous iteration's barrier
-    store_tile(buf);
+    store_tile(buf, kt);
     __syncthreads();
     if (kt + 1 < kr.y) load_tile(kt + 1);  // in flight during the FMAs below
 #pragma unroll
