@@ -155,3 +155,38 @@ def test_bounded_wait_reports_timeout_and_context_survives(srw):
     with srw.Likelihood(wl, workloads.load_counts(wl["name"])) as lk:
         v = lk.loglik(np.zeros((2, 5), np.float32), srw.SRW_BF16X3)
     assert np.all(np.isfinite(v))
+
+
+def test_single_point_bands_longer_than_a_stage(srw):
+    """The banded single-point GEMV on rows whose nonzero bands range from a few
+    hundred floats to more than one 4096-float ring stage (a band longer than a
+    stage is cut into stage-sized segments, short bands share a stage): values
+    equal the FP64 oracle's, and the bytes streamed are exactly the bands."""
+    rng = np.random.default_rng(11)
+    n_t, n_rec = 8001, 301
+    t_edges = np.linspace(0.0, 1.4, n_t + 1)
+    rec_edges = np.linspace(0.0, 1.4, n_rec + 1)
+    wl = small_workload(seed=6)
+    wl.update({"name": "long_bands", "t_edges": t_edges, "rec_edges": rec_edges,
+               "R": workloads.solar.response_matrix(t_edges, rec_edges, res=0.06),
+               "bkg": rng.uniform(0.0, 30.0, (2, n_rec))})
+    lens = []
+    for row in wl["R"]:
+        nz = np.nonzero(row)[0]
+        lens.append(nz[-1] + 1 - nz[0] if len(nz) else 0)
+    assert max(lens) > 4096 and min(lens) < 2048  # bands cut across stages and bands that share one
+    counts = _asimov(wl)
+    ref = _oracle(wl, counts)
+    th = np.concatenate([np.zeros((1, 5), np.float32), workloads.theta_box(3, 7, eps_max=0.05, mu_max=1.0)])
+    with srw.Likelihood(wl, counts) as lk:
+        ld = lk.info()["k_pad"]
+        band = 0
+        for row in wl["R"]:
+            nz = np.nonzero(row)[0]
+            lo = nz[0] // 4 * 4 if len(nz) else 0
+            ln = min((nz[-1] + 1 - lo + 31) // 32 * 32, ld) if len(nz) else 32
+            band += 4 * ln
+        assert lk.gemv_work() == band
+        for k in range(th.shape[0]):
+            got = lk.loglik(th[k:k + 1], srw.SRW_FP32)[0]
+            assert abs(got - ref.neg2lnl(th[k].astype(np.float64))) <= 1e-4, k
