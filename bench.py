@@ -772,6 +772,19 @@ def main():
     e1.synchronize()
     single["plain_points_evals_s"] = 256e3 / e0.elapsed_time(e1)
     single["batched_over_single"] = value / world / single["loglik_cold_evals_s"]
+
+    # the batched FP32 path (SIMT FMAs, Kahan-compensated 16-term chains) on the
+    # same batch, timed the same way, beside the headline
+    fp32_batched = {}
+    if prec != srw.SRW_FP32:
+        out32 = torch.empty(P, dtype=torch.float64, device=dev)
+        call32 = lambda: lk.loglik(th, srw.SRW_FP32, out=out32, stream=stream)  # noqa: E731
+        for _ in range(2):
+            flush.add_(1.0)
+            call32()
+        ms32 = timed_steps(call32, flush, stream, 5)
+        fp32_batched = {"evals_s": P * 5 / (sum(ms32) * 1e-3), "ms_per_step": statistics.mean(ms32)}
+        fp32_batched["over_single_cold"] = fp32_batched["evals_s"] / single["loglik_cold_evals_s"]
     gpu_vals = out.cpu().numpy()
     n_fit = 8
     fit_th = fit_region_points(n_fit)
@@ -791,8 +804,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
         "config": workload_config(P, prec_name), "roofline": roofline, "e2e": e2e,
-        "gpu_launches": (3 if prec == srw.SRW_FP16X3 else 2) * args.steps, "single_point_fp32": single,
+        "gpu_launches": (3 if prec != srw.SRW_FP32 else 2) * args.steps, "single_point_fp32": single,
     }
+    if fp32_batched:
+        line["fp32_batched"] = fp32_batched
     if clk:
         line["clocks"] = clk
     if world == 1 and not args.no_grouped and prec != srw.SRW_FP32:
