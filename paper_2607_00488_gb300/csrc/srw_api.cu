@@ -920,7 +920,9 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   const float* th = theta;
   double* o = out;
   if (where == SRW_HOST) {
-    if (!all_finite(theta, (size_t)P * 5)) return fail(h, SRW_EINVAL, "theta must be finite");
+    // theta is checked for finiteness on the host while the device works (see
+    // below); every kernel takes it only in arithmetic, so a non-finite value
+    // does no harm before the call fails
     srw_status st = ensure_staging(h, P);
     if (st != SRW_OK) return st;
     // a host-pointer call reports the device status of this call only
@@ -995,6 +997,11 @@ static srw_status loglik_impl(srw_handle h, const float* theta, int P, double* o
   }
   if (st != SRW_OK) return st;
   if (where == SRW_HOST) {
+    // a non-finite theta fails the call before anything is written to out
+    if (!all_finite(theta, (size_t)P * 5)) {
+      SRW_CUDA(h, cudaStreamSynchronize(s), "sync");
+      return fail(h, SRW_EINVAL, "theta must be finite");
+    }
     SRW_CUDA(h, cudaMemcpyAsync(out, o, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, s), "download");
     bool domain = false;
     st = check_status_word(h, s, &domain);

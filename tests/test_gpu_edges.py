@@ -190,3 +190,26 @@ def test_single_point_bands_longer_than_a_stage(srw):
         for k in range(th.shape[0]):
             got = lk.loglik(th[k:k + 1], srw.SRW_FP32)[0]
             assert abs(got - ref.neg2lnl(th[k].astype(np.float64))) <= 1e-4, k
+
+
+def test_non_finite_theta_fails_and_leaves_out_untouched(srw):
+    """Host-buffer calls check theta for finiteness while the device works: a
+    NaN or inf fails the call with SRW_EINVAL before anything is written to the
+    caller's result buffer, and the handle stays usable."""
+    wl = small_workload(seed=8)
+    counts = _asimov(wl)
+    ref = _oracle(wl, counts)
+    th = workloads.theta_box(6, 9, eps_max=0.05, mu_max=1.0)
+    with srw.Likelihood(wl, counts) as lk:
+        for bad in (np.nan, np.inf):
+            for prec in ("fp32", "bf16x3", "fp16x3"):
+                for n in (1, th.shape[0]):
+                    t = th[:n].copy()
+                    t[n - 1, 2] = bad
+                    out = np.full(n, 123.0)
+                    with pytest.raises(srw.SrwError) as e:
+                        lk.loglik(t, srw.PRECISIONS[prec], out=out)
+                    assert e.value.status == srw.SRW_EINVAL
+                    assert np.all(out == 123.0)
+        got = lk.loglik(th, srw.SRW_FP32)
+    np.testing.assert_allclose(got, ref.neg2lnl_batch(th.astype(np.float64)), rtol=0, atol=1e-4)
