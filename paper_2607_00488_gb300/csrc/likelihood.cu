@@ -37,15 +37,19 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // short bands share a stage, in a segment table built at create); the rows
 // are dealt in turn to eight consumer warps, which multiply them by W (read
 // through L1), keep FP32 partial sums over at most eight float4 a lane and
-// fold them into a double-float per-lane accumulator; each lane leaves its
-// share of a row in shared memory and the epilogue adds the 32 shares.  Every
-// consumer warp releases every stage with one arrive.  Every wait is bounded
-// (see ptx.cuh); a block that gives up raises kStatusTimeout.
+// fold them into a double-float per-lane accumulator; at the end of a row two
+// shuffle rounds fold the 32 lanes into 8 shares, left in shared memory, and
+// the epilogue adds them (a full warp reduction per row was a serial chain
+// on the stream's critical path; 32 shares per row would not fit in shared
+// memory at the largest row counts).  Every consumer warp releases every
+// stage with one arrive.  Every wait is bounded (see ptx.cuh); a block that
+// gives up raises kStatusTimeout.
 // ---------------------------------------------------------------------------
 constexpr int kGvConsumers = 8;
 constexpr int kGvThreads = (kGvConsumers + 1) * 32;
 constexpr int kGvChunk = 4096;  // floats per stage (16 KB)
 constexpr int kGvStages = 6;
+constexpr int kGvShares = 8;  // shares of a row a warp leaves (its 32 lanes folded in two shuffle rounds)
 constexpr int kGvRowCost = 1024;  // floats: the fixed cost of one row's copy, see gemv_prepare
 
 // One segment of a block's stream: `len` floats (a multiple of 32) of the
@@ -69,8 +73,8 @@ __device__ __forceinline__ GvSeg gv_dense(int i, int ld, int chunk) {
   return {i / per_row, k0, min(chunk, ld - k0), 0, i, part == per_row - 1};
 }
 
-// Row stride of the per-lane row partials [lane][row]: odd, so that the 32
-// lanes of a warp write to different banks.
+// Row stride of the per-row shares [share][row]: odd, so that the shares of a
+// row land in different banks.
 __host__ __device__ constexpr int gv_part_stride(int rows) { return rows | 1; }
 
 __global__ void __launch_bounds__(kGvThreads, 1)
@@ -86,7 +90,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   const int ps = gv_part_stride(rows_per_block);
   float* sbuf = reinterpret_cast<float*>(dsmem);
   float2* spart = reinterpret_cast<float2*>(dsmem + sizeof(float) * (size_t)kGvStages * chunk);
-  int4* sseg = reinterpret_cast<int4*>(spart + (size_t)32 * ps);
+  int4* sseg = reinterpret_cast<int4*>(spart + (size_t)kGvShares * ps);
   __shared__ __align__(8) uint64_t full[kGvStages], empty[kGvStages], never;
   __shared__ unsigned abort_flag;
   __shared__ double sred[kGvThreads / 32];
@@ -94,7 +98,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // rows of this block: an even split, or (row_start) a split that balances
-  // the bytes of the rows' nonzero bands
+  // the blocks' estimated stream times (see gemv_prepare)
   const int r0 = row_start ? row_start[blockIdx.x] : blockIdx.x * rows_per_block;
   const int r1 = row_start ? row_start[blockIdx.x + 1] : min(n_rec, r0 + rows_per_block);
   const int nrows = r1 > r0 ? r1 - r0 : 0;
@@ -206,9 +210,11 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
         }
         lacc = df_add(lacc, (ax + ay) + (az + aw));
       }
-      if (g.done) {  // each lane leaves its share of the row; the epilogue adds the 32
+      if (g.done) {  // two shuffle rounds fold the lanes into 8 shares; the epilogue adds them
         SRW_CHECK(status, g.row < rows_per_block);
-        spart[(size_t)lane * ps + g.row] = make_float2(lacc.hi, lacc.lo);
+        lacc = df_add(lacc, df_shfl_xor(lacc, 16));
+        lacc = df_add(lacc, df_shfl_xor(lacc, 8));
+        if (lane < kGvShares) spart[(size_t)lane * ps + g.row] = make_float2(lacc.hi, lacc.lo);
         lacc = {0.f, 0.f};
       }
     }
@@ -225,8 +231,8 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   if (abort_flag == 0u) {
     for (int rl = threadIdx.x; rl < nrows; rl += kGvThreads) {
       const int j = r0 + rl;
-      dfloat ms = {0.f, 0.f};  // the row's sum: the 32 lane shares of its warp
-      for (int l = 0; l < 32; ++l) {
+      dfloat ms = {0.f, 0.f};  // the row's sum: the shares its warp left
+      for (int l = 0; l < kGvShares; ++l) {
         const float2 v = spart[(size_t)l * ps + rl];
         ms = df_add(ms, dfloat{v.x, v.y});
       }
@@ -353,7 +359,8 @@ int fold_point_grid(const srw_ctx* h) {
 
 static size_t gv_smem(const srw_ctx* h) {
   const int chunk = h->ld_r < kGvChunk ? h->ld_r : kGvChunk;
-  return sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * 32 * (size_t)gv_part_stride(gv_rows_per_block(h)) +
+  return sizeof(float) * (size_t)kGvStages * chunk +
+         sizeof(float2) * kGvShares * (size_t)gv_part_stride(gv_rows_per_block(h)) +
          sizeof(int4) * (size_t)(h->gv_blocks > 0 ? h->gv_max_segs : 0);
 }
 
@@ -607,7 +614,8 @@ extern "C" srw_status srw_loglik_point_noalloc(const float* R, int n_rec, int ld
   const int grid = (n_rec + rpb - 1) / rpb;
   if (grid > kNoAllocMaxBlocks) return bad("too many blocks for the scratch array");
   const int chunk = ld < kGvChunk ? ld : kGvChunk;
-  const size_t smem = sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * 32 * (size_t)gv_part_stride(rpb);
+  const size_t smem =
+      sizeof(float) * (size_t)kGvStages * chunk + sizeof(float2) * kGvShares * (size_t)gv_part_stride(rpb);
   if (smem > 200 * 1024) return bad("n_rec too large for the fold's shared memory");
   cudaStream_t s = (cudaStream_t)stream;
   NoAllocScratch* sc = nd.scratch;
