@@ -671,7 +671,7 @@ static srw_status create_impl(const srw_binning* bin, const srw_source* sources,
   cudaDeviceProp prop;
   if ((ce = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return fail(nullptr, SRW_ECUDA, "device properties");
   if (!(prop.major == 10 && prop.minor == 3))
-    return fail(nullptr, SRW_EUNSUPPORTED, "this build targets sm_103a (GB300); device is sm_" +
+    return fail(nullptr, SRW_EUNSUPPORTED, "libsrw is compiled for sm_103a (GB300); device is sm_" +
                                                std::to_string(prop.major) + std::to_string(prop.minor));
 
   srw_ctx* h = new (std::nothrow) srw_ctx();
