@@ -203,7 +203,10 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
  * into its epilogue) in the requested precision.  Each distinct
  * (path, precision, P, theta, out, stream) call signature is captured once
  * into a CUDA graph and replayed.
- * Returns SRW_EDOMAIN (host calls only) when a point's value is +inf. */
+ * Returns SRW_EDOMAIN (host calls only) when a point's value is +inf.
+ * Host calls return SRW_EINVAL for a non-finite theta (checked on the host
+ * while the device computes) and then leave out untouched.  Page-locked
+ * host buffers make the copies asynchronous; pageable ones work too. */
 srw_status srw_loglik(srw_handle h, const float* theta, int P, double* out, int where,
                       srw_precision precision, void* stream);
 
