@@ -206,6 +206,64 @@ def _stream(stream):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+# The library takes every size from its integer arguments and the handle, so
+# the buffers behind the pointers are checked here, before any call.
+def _device_args(named):
+    """Each (name, tensor, dtype, minimum number of values) must be a
+    contiguous CUDA tensor of that dtype holding at least that many values,
+    all on one device; ValueError otherwise."""
+    devices = set()
+    for name, t, dtype, n_min in named:
+        if not _is_device(t):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if str(t.dtype) != "torch." + dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, str(t.dtype).replace("torch.", "")))
+        if t.numel() < n_min:
+            raise ValueError("%s holds %d values, the call needs %d" % (name, t.numel(), n_min))
+        devices.add(t.device)
+    if len(devices) > 1:
+        raise ValueError("all tensors must be on one device")
+
+
+def _device_points(theta):
+    """Number of points in a device theta (float32, 5 values a point)."""
+    _device_args([("theta", theta, "float32", 0)])
+    if theta.numel() % 5 != 0:
+        raise ValueError("theta must hold 5 values a point, got %d values" % theta.numel())
+    return theta.numel() // 5
+
+
+def _device_out(out, like, n, dtype):
+    """`out`, or a new tensor of n values on `like`'s device."""
+    if out is None:
+        import torch
+        out = torch.empty(n, dtype=getattr(torch, dtype), device=like.device)
+    return out
+
+
+def _host_out(out, n, dtype, name="out"):
+    """`out` (a writeable C-contiguous numpy array of `dtype` holding at least
+    n values), or a new one; ValueError otherwise."""
+    if out is None:
+        return np.empty(n, dtype=dtype)
+    if not isinstance(out, np.ndarray) or out.dtype != np.dtype(dtype):
+        raise ValueError("%s must be a numpy %s array" % (name, dtype))
+    if not (out.flags.c_contiguous and out.flags.writeable):
+        raise ValueError("%s must be writeable and contiguous" % name)
+    if out.size < int(np.prod(n)):
+        raise ValueError("%s holds %d values, the call needs %d" % (name, out.size, int(np.prod(n))))
+    return out
+
+
+def _spectrum_len(h, stage):
+    if int(stage) not in (0, 1, 2, 3):
+        raise ValueError("stage must be 0, 1, 2 or 3, got %r" % (stage,))
+    info = srw_info(h)
+    return info["n_t"] if int(stage) <= 1 else info["n_rec"]
+
+
 # ------------------------------------------------------------------ entry points
 def _sources(sources, keep):
     srcs = (_Source * len(sources))()
@@ -305,15 +363,18 @@ def srw_set_data(h, counts, bkg=None, mask=None):
 
 def srw_spectrum(h, theta, stage, out=None, stream=None):
     """Spectrum stage 0..3 at one point.  Host theta -> numpy result; device
-    theta (CUDA tensor) -> result written into ``out`` (CUDA float32 tensor)."""
+    theta (CUDA tensor) -> result written into ``out`` (CUDA float32 tensor,
+    allocated when None)."""
+    n = _spectrum_len(h, stage)
     if _is_device(theta):
+        _device_args([("theta", theta, "float32", 5)])
+        out = _device_out(out, theta, n, "float32")
+        _device_args([("theta", theta, "float32", 5), ("out", out, "float32", n)])
         _check(lib().srw_spectrum(h, ctypes.c_void_p(theta.data_ptr()), int(stage), ctypes.c_void_p(out.data_ptr()),
                                   SRW_DEVICE, _stream(stream)), h)
         return out
     th = np.ascontiguousarray(theta, dtype=np.float32).reshape(5)
-    info = srw_info(h)
-    n = info["n_t"] if stage <= 1 else info["n_rec"]
-    res = np.empty(n, dtype=np.float32) if out is None else out
+    res = _host_out(out, n, np.float32)
     _check(lib().srw_spectrum(h, th.ctypes.data_as(ctypes.c_void_p), int(stage), res.ctypes.data_as(ctypes.c_void_p),
                               SRW_HOST, None), h)
     return res
@@ -321,7 +382,9 @@ def srw_spectrum(h, theta, stage, out=None, stream=None):
 
 def _loglik(fn, h, theta, precision, out, stream, extra_prec=True):
     if _is_device(theta):
-        P = theta.numel() // 5
+        P = _device_points(theta)
+        out = _device_out(out, theta, P, "float64")
+        _device_args([("theta", theta, "float32", 5 * P), ("out", out, "float64", P)])
         args = [h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()), SRW_DEVICE]
         if extra_prec:
             args.append(int(precision))
@@ -330,7 +393,7 @@ def _loglik(fn, h, theta, precision, out, stream, extra_prec=True):
         return out
     th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
     P = th.shape[0]
-    res = np.empty(P, dtype=np.float64) if out is None else out
+    res = _host_out(out, P, np.float64)
     args = [h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p), SRW_HOST]
     if extra_prec:
         args.append(int(precision))
@@ -353,19 +416,27 @@ def srw_loglik_points(h, theta, out=None, stream=None):
 
 
 def srw_loglik_linear(h, theta, out=None, grad=False, grad_out=None, stream=None):
-    """Exact rank-8 evaluation: -2 ln L for P points (and, with grad=True, the
-    gradient [P, 5]).  Host theta -> numpy results; CUDA tensors -> written into
-    out (and grad_out)."""
+    """Exact rank-8 evaluation: -2 ln L for P points (and, with grad=True or a
+    grad_out, the gradient [P, 5]).  Host theta -> numpy results; CUDA tensors
+    -> written into out (and grad_out), allocated when None."""
     if _is_device(theta):
-        P = theta.numel() // 5
+        P = _device_points(theta)
+        out = _device_out(out, theta, P, "float64")
+        if grad and grad_out is None:
+            grad_out = _device_out(None, theta, 5 * P, "float64").view(P, 5)
+        named = [("theta", theta, "float32", 5 * P), ("out", out, "float64", P)]
+        if grad_out is not None:
+            named.append(("grad_out", grad_out, "float64", 5 * P))
+        _device_args(named)
         gp = ctypes.c_void_p(grad_out.data_ptr()) if grad_out is not None else None
         _check(lib().srw_loglik_linear(h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()), gp,
                                        SRW_DEVICE, _stream(stream)), h)
         return (out, grad_out) if grad_out is not None else out
     th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
     P = th.shape[0]
-    res = np.empty(P, dtype=np.float64)
-    g = np.empty((P, 5), dtype=np.float64) if grad else None
+    res = _host_out(out, P, np.float64)
+    grad = grad or grad_out is not None
+    g = _host_out(grad_out, (P, 5), np.float64, "grad_out") if grad else None
     st = lib().srw_loglik_linear(h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p),
                                  g.ctypes.data_as(ctypes.c_void_p) if grad else None, SRW_HOST, None)
     if st != SRW_EDOMAIN:
@@ -390,15 +461,19 @@ def srw_loglik_profiled(h, theta, sigma_alpha=0.0):
 
 def srw_spectrum_batch(h, theta, precision=SRW_FP32, out=None, stream=None):
     """Folded signal spectra [P, n_rec] (float32) from the batched fold."""
+    n_rec = srw_info(h)["n_rec"]
     if _is_device(theta):
-        P = theta.numel() // 5
+        P = _device_points(theta)
+        out = _device_out(out, theta, P * n_rec, "float32")
+        if out.dim() == 1 and out.numel() == P * n_rec:
+            out = out.view(P, n_rec)
+        _device_args([("theta", theta, "float32", 5 * P), ("out", out, "float32", P * n_rec)])
         _check(lib().srw_spectrum_batch(h, ctypes.c_void_p(theta.data_ptr()), P, ctypes.c_void_p(out.data_ptr()),
                                         SRW_DEVICE, int(precision), _stream(stream)), h)
         return out
     th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
     P = th.shape[0]
-    n_rec = srw_info(h)["n_rec"]
-    res = np.empty((P, n_rec), dtype=np.float32) if out is None else out
+    res = _host_out(out, (P, n_rec), np.float32)
     _check(lib().srw_spectrum_batch(h, th.ctypes.data_as(ctypes.c_void_p), P, res.ctypes.data_as(ctypes.c_void_p),
                                     SRW_HOST, int(precision), None), h)
     return res
@@ -587,14 +662,23 @@ def srw_group_create(handles, P):
     return g
 
 
-def srw_group_loglik(g, theta, precision=SRW_BF16X3, out=None, stream=None):
-    """-2 ln L of all points of all configurations (theta: sum(P) x 5, concatenated)."""
+def srw_group_loglik(g, theta, precision=SRW_BF16X3, out=None, stream=None, n_points=None):
+    """-2 ln L of all points of all configurations (theta: sum(P) x 5,
+    concatenated).  The library reads sum(P) points: pass that as n_points
+    (GroupedLikelihood does) to have theta's and out's lengths checked."""
     if _is_device(theta):
+        P = _device_points(theta)
+        if n_points is not None and P != n_points:
+            raise ValueError("theta holds %d points, the group %d" % (P, n_points))
+        out = _device_out(out, theta, P, "float64")
+        _device_args([("theta", theta, "float32", 5 * P), ("out", out, "float64", P)])
         _gcheck(lib().srw_group_loglik(g, ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                        SRW_DEVICE, int(precision), _stream(stream)), g)
         return out
     th = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1, 5)
-    res = np.empty(th.shape[0], dtype=np.float64) if out is None else out
+    if n_points is not None and th.shape[0] != n_points:
+        raise ValueError("theta holds %d points, the group %d" % (th.shape[0], n_points))
+    res = _host_out(out, th.shape[0], np.float64)
     st = lib().srw_group_loglik(g, th.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
                                 SRW_HOST, int(precision), None)
     if st == SRW_EDOMAIN:
@@ -821,7 +905,7 @@ class GroupedLikelihood:
         return np.concatenate([[0], np.cumsum(self.P)]).astype(np.int64)
 
     def loglik(self, theta, precision=SRW_BF16X3, out=None, stream=None):
-        return srw_group_loglik(self.handle, theta, precision, out, stream)
+        return srw_group_loglik(self.handle, theta, precision, out, stream, n_points=sum(self.P))
 
     def autotune(self, precision, stream=None):
         return srw_group_autotune(self.handle, precision, stream)
