@@ -31,7 +31,12 @@
  *     the result is in host memory.  `where` = SRW_DEVICE: pointers are
  *     device memory on the handle's device, and the call is asynchronous,
  *     stream-ordered on `stream` (a cudaStream_t; NULL = a stream owned by
- *     the handle, synchronised before return).
+ *     the handle, synchronised before return).  Any other `where` value, a
+ *     NULL handle or required pointer, a point count below 1 or a precision
+ *     outside srw_precision returns SRW_EINVAL before any device work; a
+ *     likelihood call on a handle without srw_set_data returns SRW_ENODATA.
+ *     The sizes of the caller's buffers are not known to the library: they
+ *     must hold what the call's arguments say it reads and writes.
  *   - No C++ exception crosses this boundary.  Every call returns a status;
  *     srw_last_error() gives a message for the last failure on a handle.
  *   - A handle is not thread-safe: use one host thread (and one stream) per

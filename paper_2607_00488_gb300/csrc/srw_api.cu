@@ -863,6 +863,7 @@ srw_status srw_spectrum(srw_handle h, const float* theta, int stage, float* out,
   if (!h) return fail(nullptr, SRW_EINVAL, "NULL handle");
   if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
   if (stage < 0 || stage > 3) return fail(h, SRW_EINVAL, "stage must be 0..3");
+  if (where != SRW_HOST && where != SRW_DEVICE) return fail(h, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
   if (stage == 3 && !h->has_data) return fail(h, SRW_ENODATA, "stage 3 needs srw_set_data");
   cudaStream_t s = pick_stream(h, stream);
   const float* th = theta;
@@ -1121,6 +1122,7 @@ srw_status srw_spectrum_batch(srw_handle h, const float* theta, int P, float* ou
   if (!theta || !out) return fail(h, SRW_EINVAL, "theta/out is NULL");
   if (P < 1) return fail(h, SRW_EINVAL, "P must be >= 1");
   if (precision < SRW_FP32 || precision > SRW_FP16X3) return fail(h, SRW_EINVAL, "bad precision");
+  if (where != SRW_HOST && where != SRW_DEVICE) return fail(h, SRW_EINVAL, "where must be SRW_HOST or SRW_DEVICE");
   if (precision != SRW_FP32 && !h->tensor_ok)
     return fail(h, SRW_EUNSUPPORTED, "tensor-core fold unavailable on this device");
   cudaStream_t s = pick_stream(h, stream);
