@@ -102,6 +102,19 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   const int r0 = row_start ? row_start[blockIdx.x] : blockIdx.x * rows_per_block;
   const int r1 = row_start ? row_start[blockIdx.x + 1] : min(n_rec, r0 + rows_per_block);
   const int nrows = r1 > r0 ? r1 - r0 : 0;
+  // The epilogue's inputs of a thread's first row (row threadIdx.x) do not
+  // depend on W: they are loaded here, so that their cold misses pass while R
+  // streams instead of after it; rows beyond the block size load later.
+  double ep_ref = 0.0, ep_b = 0.0, ep_n = 0.0, ep_c = 0.0;
+  bool ep_on = true;
+  if ((int)threadIdx.x < nrows) {
+    const int j = r0 + threadIdx.x;
+    if (muref != nullptr) ep_ref = __ldg(muref + j);
+    if (b64 != nullptr) ep_b = __ldg(b64 + j);
+    if (mask != nullptr) ep_on = __ldg(mask + j) != 0;
+    if (out != nullptr) ep_n = __ldg(n64 + j);
+  }
+  if (out != nullptr && threadIdx.x == 0) ep_c = __ldg(c_data);  // used by the last block
   // the block's segments: from the create-time table (each row's nonzero
   // band, outside which R is exactly zero, short bands packed several to a
   // stage), staged in shared memory so that no walk waits on global memory;
@@ -236,14 +249,16 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
         const float2 v = spart[(size_t)l * ps + rl];
         ms = df_add(ms, dfloat{v.x, v.y});
       }
+      const bool first = rl == (int)threadIdx.x;  // the row whose inputs are loaded
       // delta mode: W holds W(theta) - W_ref, and the FP64 reference fold is added back
-      const double musig = (double)ms.hi + (double)ms.lo + (muref != nullptr ? muref[j] : 0.0);
-      const bool on = mask == nullptr || mask[j] != 0;
-      const double mu = on ? musig + (b64 != nullptr ? b64[j] : 0.0) : 0.0;
+      const double ref = first ? ep_ref : (muref != nullptr ? muref[j] : 0.0);
+      const double musig = (double)ms.hi + (double)ms.lo + ref;
+      const bool on = first ? ep_on : (mask == nullptr || mask[j] != 0);
+      const double mu = on ? musig + (first ? ep_b : (b64 != nullptr ? b64[j] : 0.0)) : 0.0;
       if (musig_out) musig_out[j] = (float)musig;
       if (mu_out) mu_out[j] = (float)mu;
       if (on && out) {
-        const double tj = poisson_term_f64(mu, n64[j]);
+        const double tj = poisson_term_f64(mu, first ? ep_n : n64[j]);
         if (isinf(tj)) atomicOr(status, kStatusDomain);
         t += tj;
       }
@@ -274,7 +289,7 @@ fold_point_kernel(const float* __restrict__ R, int n_rec, int ld, int rows_per_b
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int w = 0; w < kGvThreads / 32; ++w) tot += sred[w];
-    out[0] = 2.0 * tot + *c_data;
+    out[0] = 2.0 * tot + ep_c;
     *ticket = 0u;
   }
 }
