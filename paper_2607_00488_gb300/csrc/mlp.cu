@@ -761,6 +761,46 @@ void sfree(T*& p) {
   p = nullptr;
 }
 
+// A device buffer owned by one call, released on every return path (through
+// the stream's pool when it was allocated stream-ordered).
+template <class T>
+struct CallBuf {
+  T* p = nullptr;
+  cudaStream_t stream = nullptr;  // set for stream-ordered allocations
+  CallBuf() = default;
+  CallBuf(const CallBuf&) = delete;
+  CallBuf& operator=(const CallBuf&) = delete;
+  ~CallBuf() {
+    if (!p) return;
+    if (stream) cudaFreeAsync(p, stream);
+    else cudaFree(p);
+  }
+};
+template <class T>
+cudaError_t salloc(CallBuf<T>* b, size_t n) {
+  return salloc(&b->p, n);
+}
+template <class T>
+cudaError_t salloc_async(CallBuf<T>* b, size_t n, cudaStream_t st) {
+  b->stream = st;
+  return srw::dev_malloc_async(&b->p, sizeof(T) * (n ? n : 1), st);
+}
+
+// CUDA events of one call, destroyed on every return path.
+template <int N>
+struct CallEvents {
+  cudaEvent_t e[N] = {};
+  CallEvents() {
+    for (auto& x : e) cudaEventCreate(&x);
+  }
+  CallEvents(const CallEvents&) = delete;
+  CallEvents& operator=(const CallEvents&) = delete;
+  ~CallEvents() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
 int round_up(long long x, int m) { return (int)((x + m - 1) / m * m); }
 
 void free_batch(SurrogateBatch* B) {
@@ -1159,8 +1199,9 @@ srw_status srw_surrogate_forward(srw_surrogate s, const float* theta, int P, flo
   SurrogateBatch* B = nullptr;
   srw_status st = get_batch(s, M, false, &B);
   if (st != SRW_OK) return st;
-  float* d_th = nullptr;
-  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
+  CallBuf<float> th;
+  S_CUDA(s, salloc_async(&th, (size_t)5 * P, s->stream), "alloc");
+  float* d_th = th.p;
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   cudaError_t e = cudaSuccess;
   if (!B->y) {  // the FP32 output buffer exists only for this hook
@@ -1176,7 +1217,6 @@ srw_status srw_surrogate_forward(srw_surrogate s, const float* theta, int P, flo
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(y, sizeof(float) * s->n_out, B->y, sizeof(float) * s->n_out_pad, sizeof(float) * s->n_out, P,
                           cudaMemcpyDeviceToHost, s->stream);
-  cudaFreeAsync(d_th, s->stream);
   if (e != cudaSuccess) return scuda(s, e, "surrogate forward");
   return check_status(s, s->stream);
 }
@@ -1188,9 +1228,10 @@ srw_status srw_surrogate_gradients(srw_surrogate s, const float* theta, const fl
   SurrogateBatch* B = nullptr;
   srw_status st = get_batch(s, M, true, &B);
   if (st != SRW_OK) return st;
-  float *d_th = nullptr, *d_t = nullptr;
-  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
-  S_CUDA(s, srw::dev_malloc_async(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
+  CallBuf<float> th, tg;
+  S_CUDA(s, salloc_async(&th, (size_t)5 * P, s->stream), "alloc");
+  S_CUDA(s, salloc_async(&tg, (size_t)M * s->n_out_pad, s->stream), "alloc");
+  float *d_th = th.p, *d_t = tg.p;
   S_CUDA(s, cudaMemsetAsync(d_t, 0, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "zero");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   S_CUDA(s, cudaMemcpy2DAsync(d_t, sizeof(float) * s->n_out_pad, targets, sizeof(float) * s->n_out,
@@ -1200,8 +1241,6 @@ srw_status srw_surrogate_gradients(srw_surrogate s, const float* theta, const fl
   double sse = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&sse, B->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFreeAsync(d_th, s->stream);
-  cudaFreeAsync(d_t, s->stream);
   if (e != cudaSuccess) return scuda(s, e, "surrogate gradients");
   st = check_status(s, s->stream);
   if (st != SRW_OK) return st;
@@ -1229,9 +1268,10 @@ srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const f
   SurrogateBatch* B = nullptr;
   srw_status st = get_batch(s, M, true, &B);
   if (st != SRW_OK) return st;
-  float *d_th = nullptr, *d_t = nullptr;
-  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, s->stream), "alloc");
-  S_CUDA(s, srw::dev_malloc_async(&d_t, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "alloc");
+  CallBuf<float> th, tg;
+  S_CUDA(s, salloc_async(&th, (size_t)5 * P, s->stream), "alloc");
+  S_CUDA(s, salloc_async(&tg, (size_t)M * s->n_out_pad, s->stream), "alloc");
+  float *d_th = th.p, *d_t = tg.p;
   S_CUDA(s, cudaMemsetAsync(d_t, 0, sizeof(float) * (size_t)M * s->n_out_pad, s->stream), "zero");
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, s->stream), "upload");
   S_CUDA(s, cudaMemcpy2DAsync(d_t, sizeof(float) * s->n_out_pad, targets, sizeof(float) * s->n_out,
@@ -1242,8 +1282,6 @@ srw_status srw_surrogate_train_step(srw_surrogate s, const float* theta, const f
   double sse = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&sse, B->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFreeAsync(d_th, s->stream);
-  cudaFreeAsync(d_t, s->stream);
   if (e != cudaSuccess) return scuda(s, e, "surrogate train step");
   if (loss) *loss = sse / ((double)P * s->n_out);
   return check_status(s, s->stream);
@@ -1368,16 +1406,16 @@ srw_status srw_surrogate_loglik(srw_surrogate s, const float* theta, int P, doub
     return r;
   }
   if (!srw::all_finite(theta, (size_t)((long long)P * 5))) return sfail(s, SRW_EINVAL, "theta must be finite");
-  float* d_th = nullptr;
-  double* d_out = nullptr;
-  S_CUDA(s, srw::dev_malloc_async(&d_th, sizeof(float) * 5 * (size_t)P, st), "alloc");
-  S_CUDA(s, srw::dev_malloc_async(&d_out, sizeof(double) * (size_t)P, st), "alloc");
+  CallBuf<float> th;
+  CallBuf<double> vo;
+  S_CUDA(s, salloc_async(&th, (size_t)5 * P, st), "alloc");
+  S_CUDA(s, salloc_async(&vo, (size_t)P, st), "alloc");
+  float* d_th = th.p;
+  double* d_out = vo.p;
   S_CUDA(s, cudaMemcpyAsync(d_th, theta, sizeof(float) * 5 * (size_t)P, cudaMemcpyHostToDevice, st), "upload");
   srw_status r = loglik_device<double>(s, d_th, P, d_out, st);
   if (r == SRW_OK)
     S_CUDA(s, cudaMemcpyAsync(out, d_out, sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, st), "download");
-  cudaFreeAsync(d_th, st);
-  cudaFreeAsync(d_out, st);
   if (r != SRW_OK) return r;
   return check_status(s, st);
 }
@@ -1391,16 +1429,18 @@ srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long 
   float4 lo0, w0;
   float lo4, w4;
   box_of(s, &lo0, &lo4, &w0, &w4);
-  float* d_th = nullptr;
-  double *d_v = nullptr, *d_o = nullptr;
-  unsigned long long* d_best = nullptr;
-  S_CUDA(s, salloc(&d_th, (size_t)kChunk * 5), "alloc");
-  S_CUDA(s, salloc(&d_v, (size_t)n_points), "alloc");
-  S_CUDA(s, salloc(&d_o, (size_t)kChunk), "alloc");
-  S_CUDA(s, salloc(&d_best, 2), "alloc");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  CallBuf<float> b_th;
+  CallBuf<double> b_v, b_o;
+  CallBuf<unsigned long long> b_best;
+  S_CUDA(s, salloc(&b_th, (size_t)kChunk * 5), "alloc");
+  S_CUDA(s, salloc(&b_v, (size_t)n_points), "alloc");
+  S_CUDA(s, salloc(&b_o, (size_t)kChunk), "alloc");
+  S_CUDA(s, salloc(&b_best, 2), "alloc");
+  float* d_th = b_th.p;
+  double *d_v = b_v.p, *d_o = b_o.p;
+  unsigned long long* d_best = b_best.p;
+  CallEvents<2> ev;
+  cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
   cudaEventRecord(e0, st);
   srw_status r = SRW_OK;
   for (long long off = 0; off < n_points && r == SRW_OK; off += kChunk) {
@@ -1422,12 +1462,6 @@ srw_status srw_surrogate_scan_exact(srw_surrogate s, long long first, long long 
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   float t = 0.f;
   cudaEventElapsedTime(&t, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  sfree(d_th);
-  sfree(d_v);
-  sfree(d_o);
-  sfree(d_best);
   if (r != SRW_OK) return sfail(s, r, std::string("exact scan: ") + srw_last_error(s->h));
   if (e != cudaSuccess) return scuda(s, e, "exact scan");
   double v;
@@ -1450,10 +1484,12 @@ srw_status exact_min_of(srw_surrogate s, const long long* d_idx, long long count
   *best_value = INFINITY;
   *best_index = -1;
   if (count <= 0) return SRW_OK;
-  double* d_ex = nullptr;
-  unsigned long long* d_best = nullptr;
-  S_CUDA(s, salloc(&d_ex, (size_t)count), "alloc");
-  S_CUDA(s, salloc(&d_best, 2), "alloc");
+  CallBuf<double> b_ex;
+  CallBuf<unsigned long long> b_best;
+  S_CUDA(s, salloc(&b_ex, (size_t)count), "alloc");
+  S_CUDA(s, salloc(&b_best, 2), "alloc");
+  double* d_ex = b_ex.p;
+  unsigned long long* d_best = b_best.p;
   srw_status r = SRW_OK;
   for (long long off = 0; off < count && r == SRW_OK; off += kChunk) {
     const int cnt = (int)std::min<long long>(kChunk, count - off);
@@ -1473,8 +1509,6 @@ srw_status exact_min_of(srw_surrogate s, const long long* d_idx, long long count
     if (e == cudaSuccess) e = cudaMemcpy(best_index, d_idx + best[1], sizeof(long long), cudaMemcpyDeviceToHost);
   }
   cudaStreamSynchronize(st);
-  sfree(d_ex);
-  sfree(d_best);
   if (r != SRW_OK) return sfail(s, r, std::string("exact re-evaluation: ") + srw_last_error(s->h));
   if (e != cudaSuccess) return scuda(s, e, "exact re-evaluation");
   const long long bits = (long long)best[0];
@@ -1498,17 +1532,19 @@ srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* o, srw_scan_
   float4 lo0, w0;
   float lo4, w4;
   box_of(s, &lo0, &lo4, &w0, &w4);
-  cudaEvent_t ev[5];
-  for (auto& x : ev) cudaEventCreate(&x);
+  CallEvents<5> evs;
+  cudaEvent_t* ev = evs.e;
   cudaEventRecord(ev[0], st);
   // ---- held-out check: both paths on the check points; per-cell largest |d|
   std::vector<double> cmax(n_cells, -1.0);  // -1: no check point in the cell
   if (o->n_check > 0) {
-    float* d_c = nullptr;
-    double *d_ex = nullptr, *d_su = nullptr;
-    S_CUDA(s, salloc(&d_c, (size_t)o->n_check * 5), "alloc");
-    S_CUDA(s, salloc(&d_ex, (size_t)o->n_check), "alloc");
-    S_CUDA(s, salloc(&d_su, (size_t)o->n_check), "alloc");
+    CallBuf<float> b_c;
+    CallBuf<double> b_ex, b_su;
+    S_CUDA(s, salloc(&b_c, (size_t)o->n_check * 5), "alloc");
+    S_CUDA(s, salloc(&b_ex, (size_t)o->n_check), "alloc");
+    S_CUDA(s, salloc(&b_su, (size_t)o->n_check), "alloc");
+    float* d_c = b_c.p;
+    double *d_ex = b_ex.p, *d_su = b_su.p;
     S_CUDA(s, cudaMemcpyAsync(d_c, o->check_theta, sizeof(float) * 5 * o->n_check, cudaMemcpyHostToDevice, st), "upload");
     srw_status r = srw_loglik(s->h, d_c, o->n_check, d_ex, SRW_DEVICE, (srw_precision)o->precision, st);
     if (r == SRW_OK) r = loglik_device<double>(s, d_c, o->n_check, d_su, st);
@@ -1518,9 +1554,6 @@ srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* o, srw_scan_
       cudaMemcpyAsync(su.data(), d_su, sizeof(double) * o->n_check, cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
     }
-    sfree(d_c);
-    sfree(d_ex);
-    sfree(d_su);
     if (r != SRW_OK) return r;
     for (int i = 0; i < o->n_check; ++i) {
       const float* th = o->check_theta + (size_t)i * 5;
@@ -1541,43 +1574,35 @@ srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* o, srw_scan_
     if (o->n_check > 0 && (cmax[c] < 0.0 || cmax[c] > o->tol)) ++res->n_flagged_cells;
   cudaEventRecord(ev[1], st);
   // ---- surrogate values of every scan point
-  float* d_vals = nullptr;
-  float* d_th = nullptr;
-  double* d_o = nullptr;
-  S_CUDA(s, salloc(&d_vals, (size_t)o->n_points), "alloc scan values");
-  S_CUDA(s, salloc(&d_th, (size_t)kScanChunk * 5), "alloc");
-  S_CUDA(s, salloc(&d_o, 65536), "alloc");
-  auto cleanup = [&](unsigned* a, unsigned long long* b, long long* c, float* m) {
-    cudaStreamSynchronize(st);
-    sfree(d_vals);
-    sfree(d_th);
-    sfree(d_o);
-    sfree(a);
-    sfree(b);
-    sfree(c);
-    sfree(m);
-    for (auto& x : ev) cudaEventDestroy(x);
-  };
+  CallBuf<float> b_vals, b_th;
+  CallBuf<double> b_o;
+  S_CUDA(s, salloc(&b_vals, (size_t)o->n_points), "alloc scan values");
+  S_CUDA(s, salloc(&b_th, (size_t)kScanChunk * 5), "alloc");
+  S_CUDA(s, salloc(&b_o, 65536), "alloc");
+  float* d_vals = b_vals.p;
+  float* d_th = b_th.p;
+  double* d_o = b_o.p;
   for (long long off = 0; off < o->n_points; off += kScanChunk) {
     const int cnt = (int)std::min<long long>(kScanChunk, o->n_points - off);
     srw::sobol_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(s->d_sobol, o->first + off, cnt, lo0, lo4, w0, w4, d_th);
     const srw_status r = loglik_device<float>(s, d_th, cnt, d_vals + off, st);
-    if (r != SRW_OK) {
-      cleanup(nullptr, nullptr, nullptr, nullptr);
-      return r;
-    }
+    if (r != SRW_OK) return r;
   }
   cudaEventRecord(ev[2], st);
   // ---- threshold of the lowest keep_frac (exact radix selection on the float bits)
   const long long k = std::max<long long>(1, (long long)std::ceil(o->keep_frac * (double)o->n_points));
-  unsigned* d_hist = nullptr;
-  unsigned long long* d_cnt = nullptr;
-  long long* d_idx = nullptr;
-  float* d_margin = nullptr;
-  S_CUDA(s, salloc(&d_hist, 65536), "alloc");
-  S_CUDA(s, salloc(&d_cnt, 3), "alloc");
-  S_CUDA(s, salloc(&d_idx, (size_t)o->n_points), "alloc index list");
-  S_CUDA(s, salloc(&d_margin, (size_t)n_cells), "alloc");
+  CallBuf<unsigned> b_hist;
+  CallBuf<unsigned long long> b_cnt;
+  CallBuf<long long> b_idx;
+  CallBuf<float> b_margin;
+  S_CUDA(s, salloc(&b_hist, 65536), "alloc");
+  S_CUDA(s, salloc(&b_cnt, 3), "alloc");
+  S_CUDA(s, salloc(&b_idx, (size_t)o->n_points), "alloc index list");
+  S_CUDA(s, salloc(&b_margin, (size_t)n_cells), "alloc");
+  unsigned* d_hist = b_hist.p;
+  unsigned long long* d_cnt = b_cnt.p;
+  long long* d_idx = b_idx.p;
+  float* d_margin = b_margin.p;
   std::vector<unsigned> hist(65536);
   S_CUDA(s, cudaMemsetAsync(d_hist, 0, sizeof(unsigned) * 65536, st), "zero");
   srw::hist_hi_kernel<<<1024, 256, 0, st>>>(d_vals, o->n_points, d_hist);
@@ -1658,7 +1683,6 @@ srw_status srw_surrogate_scan(srw_surrogate s, const srw_scan_opts* o, srw_scan_
   cudaStreamSynchronize(st);
   float t[4] = {0, 0, 0, 0};
   for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
-  cleanup(d_hist, d_cnt, d_idx, d_margin);
   if (r != SRW_OK) return r;
   res->n_selected = n_sel;
   res->ms_check = t[0];

@@ -1019,13 +1019,15 @@ class Surrogate:
     def loglik(self, theta, out=None, stream=None):
         """Surrogate -2 ln L (host theta -> numpy; CUDA tensors -> written into out)."""
         if _is_device(theta):
-            P = theta.numel() // 5
+            P = _device_points(theta)
+            out = _device_out(out, theta, P, "float64")
+            _device_args([("theta", theta, "float32", 5 * P), ("out", out, "float64", P)])
             _scheck(lib().srw_surrogate_loglik(self.handle, ctypes.c_void_p(theta.data_ptr()), P,
                                                ctypes.c_void_p(out.data_ptr()), SRW_DEVICE, _stream(stream)),
                     self.handle)
             return out
         th = _f32(theta).reshape(-1, 5)
-        res = np.empty(th.shape[0], dtype=np.float64)
+        res = _host_out(out, th.shape[0], np.float64)
         _scheck(lib().srw_surrogate_loglik(self.handle, th.ctypes.data, th.shape[0], res.ctypes.data, SRW_HOST, None),
                 self.handle)
         return res

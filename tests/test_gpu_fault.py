@@ -133,3 +133,29 @@ def test_timeout_in_a_grouped_launch(srw, case):
         got = grp.loglik(tt, srw.SRW_FP16X3)
         assert np.max(np.abs(got - ww)) <= 1e-3
         grp.close()
+
+
+def test_surrogate_calls_fail_cleanly_on_allocation_faults(srw, case):
+    # an allocation that fails part-way through a call's own buffers returns
+    # the status, frees what the call had allocated, and the next call gives
+    # the same values
+    from workloads.mlp import BOX_CENTRE, BOX_HALF, init_weights
+    _, _, lk, _, _ = case
+    with srw.Surrogate(lk, init_weights(128, seed=3), BOX_CENTRE, BOX_HALF) as sg:
+        th = sg.sobol(0, 1000)
+        want = sg.loglik(th)
+        for skip in (0, 1):  # the first or the second of the call's two buffers
+            srw.srw_fault_inject("alloc", skip)
+            with pytest.raises(srw.SrwError) as ei:
+                sg.loglik(th)
+            assert ei.value.status in (ENOMEM, ECUDA)
+            assert srw.srw_fault_pending() == 0
+        np.testing.assert_array_equal(sg.loglik(th), want)
+        ref = sg.scan_exact(4096)
+        for skip in (0, 2):  # the first or the third of the scan's four buffers
+            srw.srw_fault_inject("alloc", skip)
+            with pytest.raises(srw.SrwError):
+                sg.scan_exact(4096)
+            assert srw.srw_fault_pending() == 0
+        again = sg.scan_exact(4096)
+        assert again["best_value"] == ref["best_value"] and again["best_index"] == ref["best_index"]
