@@ -148,8 +148,9 @@ void refresh_if_changed(srw_group g) {
 }
 
 srw_status ensure_parts(srw_group g, size_t n) {
-  if (n <= g->parts_cap) return SRW_OK;
+  if (n <= g->parts_cap && g->d_parts) return SRW_OK;
   gfree(g->d_parts);
+  g->parts_cap = 0;  // a growth that fails leaves no buffer: the next call allocates again
   G_CUDA(g, srw::dev_malloc(&g->d_parts, sizeof(double) * n), "grouped partial sums");
   g->parts_cap = n;
   return SRW_OK;

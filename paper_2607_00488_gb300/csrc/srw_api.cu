@@ -160,11 +160,12 @@ static cudaStream_t pick_stream(srw_ctx* h, void* stream) {
 // Grows the staging buffers for host-pointer calls; invalidates graphs that
 // referenced the old buffers.
 static srw_status ensure_staging(srw_ctx* h, int P) {
-  if (P <= h->stage_cap) return SRW_OK;
+  if (P <= h->stage_cap && h->d_theta && h->d_out) return SRW_OK;
   int cap = std::max(P, 2 * h->stage_cap);
   destroy_graphs(h);
   dfree(h->d_theta);
   dfree(h->d_out);
+  h->stage_cap = 0;  // a growth that fails leaves no buffer: the next call allocates again
   SRW_CUDA(h, dev_malloc(&h->d_theta, sizeof(float) * 5 * (size_t)cap), "staging theta");
   SRW_CUDA(h, dev_malloc(&h->d_out, sizeof(double) * (size_t)cap), "staging out");
   h->stage_cap = cap;
@@ -173,20 +174,22 @@ static srw_status ensure_staging(srw_ctx* h, int P) {
 
 // Per-point coefficient buffer of the tensor-core folds (two float4 a point).
 static srw_status ensure_coef(srw_ctx* h, int P) {
-  if (P <= h->coef_cap) return SRW_OK;
+  if (P <= h->coef_cap && h->d_coef) return SRW_OK;
   const int cap = std::max(P, 2 * h->coef_cap);
   destroy_graphs(h);
   dfree(h->d_coef);
+  h->coef_cap = 0;
   SRW_CUDA(h, dev_malloc(&h->d_coef, 2 * sizeof(float4) * (size_t)cap), "point coefficients");
   h->coef_cap = cap;
   return SRW_OK;
 }
 
 static srw_status ensure_bparts(srw_ctx* h, size_t n) {
-  if (n <= h->bpart_cap) return SRW_OK;
+  if (n <= h->bpart_cap && h->d_bpart) return SRW_OK;
   size_t cap = std::max(n, 2 * h->bpart_cap);
   destroy_graphs(h);
   dfree(h->d_bpart);
+  h->bpart_cap = 0;
   // the debug build keeps canary doubles after the buffer (checked by host-pointer calls)
   const size_t extra = kDebugChecks ? kCanaryDoubles : 0;
   SRW_CUDA(h, dev_malloc(&h->d_bpart, sizeof(double) * (cap + extra)), "batched partials");

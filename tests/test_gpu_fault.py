@@ -74,6 +74,19 @@ def test_allocation_failure_in_a_call_leaves_the_handle_usable(srw, case):
     assert np.max(np.abs(got - np.concatenate([want] * 40))) <= 1e-3
 
 
+def test_a_failed_growth_then_a_call_that_fits_the_old_size(srw, case):
+    # the failed call freed the old staging buffers before its allocation
+    # failed: a later call that fits the old capacity must allocate again
+    _, _, lk, th, want = case
+    lk.loglik(np.concatenate([th] * 2), srw.SRW_FP16X3)  # some capacity exists
+    srw.srw_fault_inject("alloc")
+    with pytest.raises(srw.SrwError) as ei:
+        lk.loglik(np.concatenate([th] * 200), srw.SRW_FP16X3)  # grows the staging buffers
+    assert ei.value.status == ENOMEM
+    _ok(lk, th[:20], want[:20], srw.SRW_FP16X3)
+    _ok(lk, th[:1], want[:1], srw.SRW_FP32)
+
+
 @pytest.mark.parametrize("prec", [0, 2, 3])
 def test_launch_failure_is_reported_and_not_cached(srw, case, prec):
     _, _, lk, th, want = case
