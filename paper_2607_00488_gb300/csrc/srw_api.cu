@@ -835,16 +835,19 @@ srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, i
     if (!(counts[j] >= 0.0) || !std::isfinite(counts[j])) return fail(h, SRW_EINVAL, "counts must be finite and >= 0");
   if (n_bkg > 0 && !finite_all(bkg, (size_t)n_bkg * n_rec)) return fail(h, SRW_EINVAL, "backgrounds must be finite");
   cudaStream_t s = h->own_stream;
-  if (!h->d_n64) {
-    SRW_CUDA(h, dalloc(h, &h->d_n64, n_rec), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_b64, n_rec), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_nbm, n_rec), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_nb2, n_rec), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_nb4, n_rec), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_cdata, 1), "alloc data");
-    SRW_CUDA(h, dalloc(h, &h->d_bref64, n_rec), "alloc data");
-  }
+  // each buffer once; after a call whose allocation failed part-way, the next
+  // call allocates the ones still missing
+  if (!h->d_n64) SRW_CUDA(h, dalloc(h, &h->d_n64, n_rec), "alloc data");
+  if (!h->d_b64) SRW_CUDA(h, dalloc(h, &h->d_b64, n_rec), "alloc data");
+  if (!h->d_nbm) SRW_CUDA(h, dalloc(h, &h->d_nbm, n_rec), "alloc data");
+  if (!h->d_nb2) SRW_CUDA(h, dalloc(h, &h->d_nb2, n_rec), "alloc data");
+  if (!h->d_nb4) SRW_CUDA(h, dalloc(h, &h->d_nb4, n_rec), "alloc data");
+  if (!h->d_cdata) SRW_CUDA(h, dalloc(h, &h->d_cdata, 1), "alloc data");
+  if (!h->d_bref64) SRW_CUDA(h, dalloc(h, &h->d_bref64, n_rec), "alloc data");
   if (mask && !h->d_mask) SRW_CUDA(h, dalloc(h, &h->d_mask, n_rec), "alloc mask");
+  // from here on the data change: a failure leaves the handle without data
+  // (SRW_ENODATA) rather than with a mix of the old and the new
+  h->has_data = 0;
   if (!mask) dfree(h->d_mask);
   destroy_graphs(h);
   double* d_bkg = nullptr;

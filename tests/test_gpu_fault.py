@@ -74,6 +74,23 @@ def test_allocation_failure_in_a_call_leaves_the_handle_usable(srw, case):
     assert np.max(np.abs(got - np.concatenate([want] * 40))) <= 1e-3
 
 
+def test_set_data_after_a_failed_first_set_data(srw, case):
+    # the first srw_set_data of a handle allocates its data buffers; when the
+    # second of them fails, the next srw_set_data allocates the rest
+    wl, counts, _, th, want = case
+    with srw.Likelihood(wl) as lk:
+        srw.srw_fault_inject("alloc", 1)
+        with pytest.raises(srw.SrwError) as ei:
+            srw.srw_set_data(lk.handle, counts, wl["bkg"])
+        assert ei.value.status == ENOMEM
+        with pytest.raises(srw.SrwError) as ei:
+            lk.loglik(th[:4], srw.SRW_FP32)
+        assert ei.value.status == 4  # SRW_ENODATA: no data yet
+        srw.srw_set_data(lk.handle, counts, wl["bkg"])
+        _ok(lk, th[:20], want[:20], srw.SRW_FP32)
+        _ok(lk, th[:20], want[:20], srw.SRW_FP16X3)
+
+
 def test_a_failed_growth_then_a_call_that_fits_the_old_size(srw, case):
     # the failed call freed the old staging buffers before its allocation
     # failed: a later call that fits the old capacity must allocate again
