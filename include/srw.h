@@ -383,7 +383,7 @@ srw_status srw_group_create(const srw_handle* handles, int n, const int* P, srw_
 /* -2 ln L of every point of every configuration.
  *   theta: (sum_g P[g]) x 5 float32, configuration 0's points first, then
  *          configuration 1's, ...;  out: sum_g P[g] float64 in the same order.
- * SRW_BF16 / SRW_BF16X3: one persistent tensor-core launch over all
+ * SRW_BF16 / SRW_BF16X3 / SRW_FP16X3: one persistent tensor-core launch over all
  * configurations (work items = 128-point x bn-bin tiles, bn = 128 or 256 per
  * configuration, assigned to CTAs longest-first onto the least-loaded CTA),
  * then one reduction launch.  SRW_FP32: the SIMT fold of each configuration
