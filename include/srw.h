@@ -187,7 +187,9 @@ srw_status srw_joint_layout(srw_handle h, int* n_columns, int* source, int* bin)
  *   bkg:    n_bkg x n_rec background templates in expected counts (summed);
  *           may be NULL when n_bkg == 0;
  *   mask:   n_rec live-bin mask M_j (0 drops the bin), or NULL for all bins.
- * Precomputes the theta-independent part of -2lnL in FP64 on the device. */
+ * Precomputes the theta-independent part of -2lnL in FP64 on the device.
+ * A call that fails after it has begun replacing the data leaves the handle
+ * without data: likelihood calls return SRW_ENODATA until a call succeeds. */
 srw_status srw_set_data(srw_handle h, const double* counts, const double* bkg, int n_bkg,
                         const unsigned char* mask);
 
