@@ -327,7 +327,9 @@ srw_status srw_info(srw_handle h, srw_info_t* info);
  * point: the folds then carry all of W(theta) in the chosen precision except
  * its theta-independent part (the nu_mu spectrum), which is folded once in
  * FP64 in every mode.
- * Synchronous; invalidates captured graphs. */
+ * Synchronous; invalidates captured graphs.  If the reference fold fails
+ * (SRW_ECUDA), the new point's coefficients are in place with the old fold:
+ * repeat the call before evaluating. */
 srw_status srw_set_reference(srw_handle h, const float* theta_ref);
 
 /* Kernel timing.  With profiling enabled, srw_loglik launches its kernels
