@@ -257,6 +257,11 @@ def _host_out(out, n, dtype, name="out"):
     return out
 
 
+def _need(cond, msg, *args):
+    if not cond:
+        raise ValueError(msg % args)
+
+
 def _spectrum_len(h, stage):
     if int(stage) not in (0, 1, 2, 3):
         raise ValueError("stage must be 0, 1, 2 or 3, got %r" % (stage,))
@@ -268,9 +273,12 @@ def _spectrum_len(h, stage):
 def _sources(sources, keep):
     srcs = (_Source * len(sources))()
     for k, s in enumerate(sources):
-        e = np.ascontiguousarray(s["e"], dtype=np.float64)
-        w = np.ascontiguousarray(s["w"], dtype=np.float64)
-        p = np.ascontiguousarray(s["pee"], dtype=np.float64)
+        e = np.ascontiguousarray(s["e"], dtype=np.float64).reshape(-1)
+        w = np.ascontiguousarray(s["w"], dtype=np.float64).reshape(-1)
+        p = np.ascontiguousarray(s["pee"], dtype=np.float64).reshape(-1)
+        _need(e.size >= 1 and w.size == e.size and p.size == e.size,
+              "source %d: e, w and pee must hold the same number (>= 1) of nodes, got %d, %d, %d", k, e.size, w.size,
+              p.size)
         keep += [e, w, p]
         srcs[k] = _Source(e.size, _dptr(e), _dptr(w), _dptr(p))
     return srcs
@@ -279,9 +287,13 @@ def _sources(sources, keep):
 def srw_create(t_edges, n_rec, sources, R, exposure, t_min=1e-3, midpoint=False, sin2w=0.23121, f_tau=0.5,
                e_true_sm=None):
     """Create a context (see srw_create in include/srw.h).  Returns the handle."""
-    L = lib()
-    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
+    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64).reshape(-1)
     R = np.ascontiguousarray(R, dtype=np.float32)
+    n_t = t_edges.size - 1
+    _need(n_t >= 1, "t_edges must hold n_t + 1 >= 2 edges")
+    _need(R.shape == (int(n_rec), n_t), "R must be n_rec x n_t = %d x %d, got %s", int(n_rec), n_t, R.shape)
+    _need(e_true_sm is None or np.size(e_true_sm) == n_t, "e_true_sm must hold n_t = %d values", n_t)
+    L = lib()
     keep = [t_edges, R]
     srcs = _sources(sources, keep)
     b = _Binning(t_edges.size - 1, _dptr(t_edges), int(n_rec), float(t_min), 1 if midpoint else 0)
@@ -303,14 +315,24 @@ def srw_create_joint(t_edges, components, hist, exposure, mask=None, scale=None,
     srw_create_joint in include/srw.h): hist[k] is component k's [n_rec, n_t]
     Monte Carlo histogram, mask[k] its live-time correction (or None)."""
     L = lib()
-    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64)
+    t_edges = np.ascontiguousarray(t_edges, dtype=np.float64).reshape(-1)
     keep = [t_edges]
     srcs = _sources(components, keep)
     n_src = len(components)
     hs = [np.ascontiguousarray(x, dtype=np.float64) for x in hist]
     if len(hs) != n_src:
         raise ValueError("one histogram per component")
+    n_t = t_edges.size - 1
+    _need(n_t >= 1 and hs[0].ndim == 2, "t_edges must hold n_t + 1 >= 2 edges and hist[0] be 2-D")
     n_rec = hs[0].shape[0]
+    for k, x in enumerate(hs):
+        _need(x.shape == (n_rec, n_t), "hist[%d] must be n_rec x n_t = %d x %d, got %s", k, n_rec, n_t, x.shape)
+    if mask is not None:
+        _need(len(mask) == n_src, "one live-time correction (or None) per component")
+        for k, m in enumerate(mask):
+            _need(m is None or np.size(m) == n_rec, "mask[%d] must hold n_rec = %d values", k, n_rec)
+    for name, a, n in (("scale", scale, n_src), ("events", events, n_src), ("live", live, n_rec)):
+        _need(a is None or np.size(a) == n, "%s must hold %d values", name, n)
     keep += hs
     dpp = ctypes.POINTER(ctypes.c_double)
     harr = (dpp * n_src)(*[_dptr(x) for x in hs])
@@ -347,16 +369,21 @@ def srw_joint_layout(h):
 
 
 def srw_set_data(h, counts, bkg=None, mask=None):
-    counts = np.ascontiguousarray(counts, dtype=np.float64)
+    n_rec = srw_info(h)["n_rec"]
+    counts = np.ascontiguousarray(counts, dtype=np.float64).reshape(-1)
+    _need(counts.size == n_rec, "counts must hold n_rec = %d values, got %d", n_rec, counts.size)
     n_bkg = 0
     bptr = None
     if bkg is not None:
         bkg = np.ascontiguousarray(np.atleast_2d(bkg), dtype=np.float64)
+        _need(bkg.ndim == 2 and bkg.shape[1] == n_rec, "bkg must be n_bkg x n_rec (n_rec = %d), got %s", n_rec,
+              bkg.shape)
         n_bkg = bkg.shape[0]
         bptr = _dptr(bkg)
     mptr = None
     if mask is not None:
-        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        _need(mask.size == n_rec, "mask must hold n_rec = %d values, got %d", n_rec, mask.size)
         mptr = mask.ctypes.data_as(ctypes.c_void_p)
     _check(lib().srw_set_data(h, _dptr(counts), bptr, n_bkg, mptr), h)
 
@@ -737,8 +764,23 @@ def _ptr_array(arrays):
     return (ctypes.c_void_p * len(arrays))(*[a.ctypes.data for a in arrays])
 
 
+_HIDDEN = 256  # the surrogate's hidden width (fixed by the library)
+
+
+def _check_weights(params, n_out):
+    """The four layers' (W, b) as the library reads them: W1 [256][5], W2 and
+    W3 [256][256], W4 [n_out][256], each b as long as its W has rows."""
+    _need(len(params) == 4, "four layers (W, b), got %d", len(params))
+    shapes = [(_HIDDEN, 5), (_HIDDEN, _HIDDEN), (_HIDDEN, _HIDDEN), (n_out, _HIDDEN)]
+    for k, ((W, b), want) in enumerate(zip(params, shapes)):
+        _need(np.shape(W) == want, "layer %d: W must be %s, got %s", k + 1, want, np.shape(W))
+        _need(np.size(b) == want[0], "layer %d: b must hold %d values, got %d", k + 1, want[0], np.size(b))
+
+
 def srw_surrogate_create(h, centre, half_width, params):
     """params: [(W, b), ...] of the four layers (float32 host arrays)."""
+    _check_weights(params, srw_info(h)["n_rec"])
+    _need(np.size(centre) == 5 and np.size(half_width) == 5, "centre and half_width must hold 5 values each")
     flat = [_f32(x) for W, b in params for x in (W, b)]
     c, hw = _f32(centre), _f32(half_width)
     out = ctypes.c_void_p()
@@ -746,7 +788,10 @@ def srw_surrogate_create(h, centre, half_width, params):
     return out
 
 
-def srw_surrogate_set_weights(sg, params):
+def srw_surrogate_set_weights(sg, params, n_out=None):
+    """Replace the weights; with n_out (the handle's n_rec) their shapes are checked."""
+    if n_out is not None:
+        _check_weights(params, n_out)
     flat = [_f32(x) for W, b in params for x in (W, b)]
     _scheck(lib().srw_surrogate_set_weights(sg, _ptr_array(flat)), sg)
 
@@ -775,6 +820,8 @@ def srw_surrogate_forward(sg, theta, n_out):
 def srw_surrogate_gradients(sg, theta, targets, shapes_like):
     th = _f32(theta).reshape(-1, 5)
     t = _f32(targets)
+    n_out = np.size(shapes_like[-1][1])
+    _need(t.size == th.shape[0] * n_out, "targets must be P x n_out = %d x %d", th.shape[0], n_out)
     flat = _like(shapes_like)
     loss = ctypes.c_double()
     _scheck(lib().srw_surrogate_gradients(sg, th.ctypes.data, t.ctypes.data, th.shape[0], _ptr_array(flat),
@@ -782,9 +829,10 @@ def srw_surrogate_gradients(sg, theta, targets, shapes_like):
     return loss.value, _pairs(flat)
 
 
-def srw_surrogate_train_step(sg, theta, targets, lr):
+def srw_surrogate_train_step(sg, theta, targets, lr, n_out=None):
     th = _f32(theta).reshape(-1, 5)
     t = _f32(targets)
+    _need(n_out is None or t.size == th.shape[0] * n_out, "targets must be P x n_out = %d x %s", th.shape[0], n_out)
     loss = ctypes.c_double()
     _scheck(lib().srw_surrogate_train_step(sg, th.ctypes.data, t.ctypes.data, th.shape[0], ctypes.c_float(lr),
                                            ctypes.byref(loss)), sg)
@@ -827,7 +875,12 @@ class Likelihood:
                                      t_min=wl["t_min"], midpoint=midpoint, sin2w=wl["sin2w"], f_tau=wl["f_tau"],
                                      e_true_sm=e_true_sm)
         if counts is not None:
-            srw_set_data(self.handle, counts, wl.get("bkg"), mask)
+            try:
+                srw_set_data(self.handle, counts, wl.get("bkg"), mask)
+            except Exception:
+                srw_destroy(self.handle)
+                self.handle = None
+                raise
 
     def spectrum(self, theta, stage, out=None, stream=None):
         return srw_spectrum(self.handle, theta, stage, out, stream)
@@ -950,7 +1003,7 @@ class Surrogate:
         self.handle = srw_surrogate_create(likelihood.handle, centre, half_width, params)
 
     def set_weights(self, params):
-        srw_surrogate_set_weights(self.handle, params)
+        srw_surrogate_set_weights(self.handle, params, self.n_out)
 
     def weights(self):
         return srw_surrogate_get_weights(self.handle, self.shapes)
@@ -962,7 +1015,7 @@ class Surrogate:
         return srw_surrogate_gradients(self.handle, theta, targets, self.shapes)
 
     def train_step(self, theta, targets, lr):
-        return srw_surrogate_train_step(self.handle, theta, targets, lr)
+        return srw_surrogate_train_step(self.handle, theta, targets, lr, self.n_out)
 
     def fit(self, theta, epochs, batch=8192, lr=1e-3, lr_final=1e-5, precision=None):
         """Train on the exact path's spectra at theta (host [n, 5]); returns the per-epoch losses."""
