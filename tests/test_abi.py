@@ -67,9 +67,10 @@ def _args(**kw):
 ])
 def test_create_rejects_invalid_arguments(srw, bad):
     a = _args(**bad)
-    r = a["R"]
-    if a["n_rec"] == 0:
-        r = np.zeros((1, 8), dtype=np.float32)
+    # R shaped n_rec x n_t, so that the binding's shape check passes and the
+    # library's own checks decide
+    n_t = a["t_edges"].size - 1
+    r = a["R"] if "R" in bad else np.full((a["n_rec"], n_t), 0.2, dtype=np.float32)
     with pytest.raises(srw.SrwError) as ei:
         srw.srw_create(a["t_edges"], a["n_rec"], a["sources"], r, a["exposure"])
     assert ei.value.status == 1  # SRW_EINVAL, raised before any device call
