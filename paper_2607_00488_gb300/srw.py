@@ -683,7 +683,8 @@ def srw_group_create(handles, P):
     """Group handles with P[g] points each (see srw_group_create in include/srw.h)."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
-    pv = np.ascontiguousarray(P, dtype=np.int32)
+    pv = np.ascontiguousarray(P, dtype=np.int32).reshape(-1)
+    _need(pv.size == n, "one point count per handle: %d handles, %d counts", n, pv.size)
     g = ctypes.c_void_p()
     _gcheck(lib().srw_group_create(hs, n, pv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(g)), None)
     return g

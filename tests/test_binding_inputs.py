@@ -168,3 +168,12 @@ def test_surrogate_refuses_wrong_weights_and_targets(fake, monkeypatch):
     with pytest.raises(ValueError, match="targets"):
         binding.srw_surrogate_train_step(h, np.zeros((3, 5)), np.zeros((2, 128)), 1e-3, n_out=128)
     assert not fake.calls
+
+
+def test_group_create_needs_one_count_per_handle(fake):
+    hs = [ctypes.c_void_p(HANDLE), ctypes.c_void_p(HANDLE + 8)]
+    with pytest.raises(ValueError, match="one point count per handle"):
+        binding.srw_group_create(hs, [4])
+    assert not fake.calls
+    binding.srw_group_create(hs, [4, 0])
+    assert fake.calls == ["srw_group_create"]
